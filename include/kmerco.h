@@ -1,0 +1,199 @@
+/*
+ * kmerco.h -- C ABI of the GB300 countBF K-mer counter (KmerCo, arXiv
+ * 2305.07545).
+ *
+ * The library counts K-mers of DNA reads in a countBF: a flat array of
+ * 64-bit cells, each holding eta = floor(64 / alpha) counters of alpha bits
+ * (Section 2.1).  It has two phases (Section 3, Fig. "Working of KmerCo"):
+ *
+ *   insertion       every K-mer window of every read is 2-bit packed,
+ *                   replaced by its canonical form and hashed by k_h seeded
+ *                   hash functions; each hash saturating-increments one
+ *                   counter (Algorithm 1, Algorithm 3);
+ *   classification  the distinct K-mers are found exactly, each is queried
+ *                   for the minimum of its k_h counters, and the distinct
+ *                   list is split into trustworthy (estimate > tau) and
+ *                   erroneous (estimate <= tau) K-mers (Algorithm 2,
+ *                   Algorithm 5).
+ *
+ * Conventions shared by every call:
+ *  - Status: every int-returning call returns KMERCO_OK (0) or one of the
+ *    KMERCO_E* codes below; kmerco_strerror() names them.  A non-zero
+ *    status leaves the handle usable unless it is KMERCO_ECUDA, after which
+ *    only kmerco_destroy() is meaningful.
+ *  - Pointers: "host or device" arguments may point to ordinary host memory,
+ *    pinned host memory, or CUDA device memory of the handle's device; the
+ *    library tells them apart with cudaPointerGetAttributes.
+ *  - Ownership: the library owns the countBF, the distinct-key set and the
+ *    classification results; the caller owns every buffer it passes and
+ *    must keep insert inputs alive until the next synchronising call
+ *    (classify, stats, any getter, reset, destroy).
+ *  - Streams: all device work of a handle runs in order on its stream
+ *    (kmerco_config_t.stream, else a private non-blocking stream).
+ *  - Threads: one handle must not be used from two host threads at once;
+ *    different handles are independent.
+ *  - Keys: a packed K-mer is sum_i code(b_i) * 4^(K-1-i) with A=0, C=1,
+ *    G=2, T=3, first base most significant.  For K <= 32 a key is one
+ *    uint64_t; for 33 <= K <= 64 it is two uint64_t words, low word first
+ *    (the little-endian layout of a 128-bit integer).  Keys are reported in
+ *    ascending numeric order, which is lexicographic order of the bases.
+ */
+#ifndef KMERCO_H
+#define KMERCO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define KMERCO_OK 0
+#define KMERCO_EINVAL 1   /* an argument is out of range or inconsistent */
+#define KMERCO_ENOMEM 2   /* device or pinned allocation failed, or the HBM budget is exceeded */
+#define KMERCO_ECUDA 3    /* a CUDA runtime call or kernel launch failed */
+#define KMERCO_ETIMEOUT 4 /* a bounded device retry loop gave up; results are incomplete */
+#define KMERCO_ESTATE 5   /* call not valid in the handle's state (e.g. a getter before classify) */
+#define KMERCO_ESIZE 6    /* the caller's buffer is too small; the required count is returned */
+
+typedef struct kmerco kmerco_t;
+
+/* Options of kmerco_create_ex().  Zero-initialise, then set fields. */
+typedef struct {
+    int k;                 /* K-mer length, 1..64 (Table 1) */
+    uint64_t m;            /* counters requested, >= 1; rounded up to a multiple of eta */
+    int counter_bits;      /* alpha, 1..32 (Section 2.1) */
+    int nhash;             /* k_h, 1..32 (Table 1) */
+    uint32_t threshold;    /* tau, must be < 2^alpha - 1 (Table 1, Algorithm 2) */
+    int forward_only;      /* 0: canonical K-mers (Section 2.3, default); 1: forward strand as read */
+    void *stream;          /* cudaStream_t to run on; NULL: the library creates its own */
+    uint64_t hbm_budget;   /* bytes of device memory the handle may hold; 0: no limit */
+    int device;            /* CUDA device ordinal; -1: the current device */
+} kmerco_config_t;
+
+/* Running totals and results of one handle (kmerco_stats). */
+typedef struct {
+    uint64_t windows;            /* sum over reads of max(0, len - K + 1) (Section 1.1) */
+    uint64_t n_skipped;          /* windows holding a byte other than ACGTacgt */
+    uint64_t inserted;           /* windows inserted into the countBF = windows - n_skipped */
+    uint64_t distinct;           /* distinct canonical K-mers inserted so far */
+    uint64_t trustworthy;        /* distinct K-mers with estimate > tau (after classify) */
+    uint64_t erroneous;          /* distinct K-mers with estimate <= tau (after classify) */
+    uint64_t saturated_counters; /* counters equal to 2^alpha - 1 */
+    uint64_t m_actual;           /* counters in the countBF (m rounded up to a multiple of eta) */
+    uint64_t words;              /* 64-bit cells: m_actual / eta */
+    uint64_t device_bytes;       /* device memory held by the handle */
+    uint64_t launches;           /* CUDA kernels this handle has launched since creation */
+    int k, counter_bits, eta, nhash;
+    uint32_t threshold;
+    int classified;              /* 1 when trustworthy/erroneous reflect every insert so far */
+    float insert_ms;             /* device time of the last kmerco_insert */
+    float classify_ms;           /* device time of the last kmerco_classify */
+} kmerco_stats_t;
+
+/*
+ * Create a countBF handle (Section 2.1 countBF; Algorithm 1 inputs K, k_h;
+ * Algorithm 2 input tau).  Equivalent to kmerco_create_ex() with
+ * canonical K-mers, a private stream, no HBM budget and the current device.
+ * The countBF (m_actual / eta cells) is allocated and zeroed.
+ * Errors: EINVAL when k, counter_bits, nhash or m is out of range or
+ * threshold >= 2^counter_bits - 1 (a counter at its maximum could no longer
+ * separate the classes; Section 3 after Algorithm 3); ENOMEM; ECUDA.
+ * On success *out receives the handle; on error *out is set to NULL.
+ */
+int kmerco_create(int k, uint64_t m, int counter_bits, int nhash, uint32_t threshold,
+                  kmerco_t **out);
+
+/* As kmerco_create() with every option of kmerco_config_t. */
+int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out);
+
+/* Release the handle and all device memory it holds.  NULL is ignored. */
+void kmerco_destroy(kmerco_t *h);
+
+/*
+ * Insertion phase (Algorithm 1 with Algorithm 3) over one batch of reads.
+ * bases:   host or device, ASCII nucleotides of all reads back to back.
+ * offsets: host or device, nreads + 1 non-decreasing uint64 indexes into
+ *          bases; read r is bases[offsets[r] .. offsets[r+1]).
+ * Every window of K bases inside one read is taken; a window holding any
+ * byte other than A, C, G, T (either case) is skipped.  Each window's
+ * canonical key (the smaller of the forward and reverse-complement packed
+ * values, Section 2.2-2.3) is hashed by H_a = MurmurHash3_x64_128 with seed
+ * a, a = 0..k_h-1, first output word; counter g = H_a mod m_actual, cell
+ * g / eta, counter g mod eta, is incremented unless it already holds
+ * 2^alpha - 1.  The key also joins the handle's distinct-key set.
+ * Calls accumulate; order of reads and calls does not change any result.
+ * Asynchronous on the handle's stream, except that device-resident offsets
+ * are read back once to size internal buffers.
+ * Errors: EINVAL (NULL pointer with nreads > 0, nreads >= 2^32 - 1,
+ * decreasing offsets); ENOMEM; ECUDA.
+ */
+int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint64_t nreads);
+
+/*
+ * Classification phase (Algorithm 2 with QcountBF-II, Algorithm 5): sort the
+ * distinct-key set ascending, estimate each key as 0 if any of its k_h
+ * counters is 0 and otherwise their minimum, and split the keys into
+ * trustworthy (estimate > tau) and erroneous (estimate <= tau), both kept in
+ * ascending order.  Synchronises.  Idempotent until the next insert.
+ * Errors: ETIMEOUT if an earlier insert's bounded retry loop gave up;
+ * EINVAL if an earlier insert found decreasing offsets; ENOMEM; ECUDA.
+ */
+int kmerco_classify(kmerco_t *h);
+
+/* Fill *s (host pointer) with the handle's totals.  Synchronises; counts
+ * saturated counters on the device.  Errors: EINVAL (NULL), ECUDA. */
+int kmerco_stats(kmerco_t *h, kmerco_stats_t *s);
+
+/*
+ * Copy the countBF cells (Section 2.1 layout: counter l of a cell in bits
+ * [alpha*l, alpha*l + alpha), wasted high bits zero) to dst (host or
+ * device).  nwords must be >= stats.words; fewer gives ESIZE.
+ */
+int kmerco_get_counters(kmerco_t *h, uint64_t *dst, uint64_t nwords);
+
+/*
+ * Copy the distinct keys (ascending) and their estimates after
+ * kmerco_classify().  keys: host or device, room for cap keys (cap * words
+ * per key uint64_t); est: host or device, cap uint32_t, or NULL.  *n
+ * receives the number of distinct keys; keys == NULL only queries it.
+ * ESTATE before classify (or after a later insert), ESIZE when cap < *n.
+ */
+int kmerco_get_distinct(kmerco_t *h, uint64_t *keys, uint32_t *est, uint64_t cap, uint64_t *n);
+
+/* Trustworthy keys (estimate > tau), ascending; same contract as
+ * kmerco_get_distinct() without estimates (Algorithm 2, trustworthy file). */
+int kmerco_get_trusted(kmerco_t *h, uint64_t *keys, uint64_t cap, uint64_t *n);
+
+/* Erroneous keys (estimate <= tau), ascending (Algorithm 2, erroneous file). */
+int kmerco_get_erroneous(kmerco_t *h, uint64_t *keys, uint64_t cap, uint64_t *n);
+
+/*
+ * QcountBF-II (Algorithm 5) for n arbitrary packed keys: est[i] = 0 when any
+ * of key i's k_h counters is zero, else their minimum.  keys and est are
+ * host or device (layout as above).  Synchronises.
+ */
+int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est);
+
+/*
+ * Merge the countBF and distinct-key set of src into dst, as if dst had also
+ * inserted src's reads: every counter becomes min(a + b, 2^alpha - 1), which
+ * equals the countBF of the union of both inputs because saturating
+ * increments commute (Algorithm 3 read per counter).  Both handles must have
+ * the same K, m, counter_bits, nhash and strand mode and the same device;
+ * src is left unchanged.  Errors: EINVAL (mismatch), ENOMEM, ECUDA.
+ */
+int kmerco_merge(kmerco_t *dst, kmerco_t *src);
+
+/* Zero the countBF, empty the distinct set and all totals; keeps memory. */
+int kmerco_reset(kmerco_t *h);
+
+/* Static description of a status code; never NULL. */
+const char *kmerco_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KMERCO_H */

@@ -1,0 +1,275 @@
+"""GB300 countBF K-mer counter (KmerCo, arXiv 2305.07545): Python binding.
+
+A thin ctypes layer over ``libkmerco.so`` (the C ABI in ``include/kmerco.h``).
+It only marshals arguments -- numpy arrays, torch tensors (CPU or CUDA) or
+raw pointers -- into the C calls, which run every step of the method in
+CUDA kernels.  There is no CPU fallback: if the library is missing and
+cannot be built, :func:`load` raises.
+
+The functions keep the C names (``kmerco_create`` ... ``kmerco_strerror``)
+and raise :class:`KmercoError` on a non-zero status; :class:`CountBF` wraps a
+handle with numpy results.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_float, c_int, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkmerco.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ESIZE = range(7)
+
+
+class kmerco_config_t(ctypes.Structure):
+    _fields_ = [("k", c_int), ("m", c_uint64), ("counter_bits", c_int), ("nhash", c_int),
+                ("threshold", c_uint32), ("forward_only", c_int), ("stream", c_void_p),
+                ("hbm_budget", c_uint64), ("device", c_int)]
+
+
+class kmerco_stats_t(ctypes.Structure):
+    _fields_ = [("windows", c_uint64), ("n_skipped", c_uint64), ("inserted", c_uint64),
+                ("distinct", c_uint64), ("trustworthy", c_uint64), ("erroneous", c_uint64),
+                ("saturated_counters", c_uint64), ("m_actual", c_uint64), ("words", c_uint64),
+                ("device_bytes", c_uint64), ("launches", c_uint64), ("k", c_int), ("counter_bits", c_int),
+                ("eta", c_int), ("nhash", c_int), ("threshold", c_uint32),
+                ("classified", c_int), ("insert_ms", c_float), ("classify_ms", c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class KmercoError(RuntimeError):
+    def __init__(self, status: int, call: str):
+        self.status = status
+        super().__init__(f"{call}: {kmerco_strerror(status)} (status {status})")
+
+
+_lib = None
+_u64p = POINTER(c_uint64)
+_u32p = POINTER(c_uint32)
+
+# Exported symbols and their signatures (restype, argtypes).
+SIGNATURES = {
+    "kmerco_create": (c_int, [c_int, c_uint64, c_int, c_int, c_uint32, POINTER(c_void_p)]),
+    "kmerco_create_ex": (c_int, [POINTER(kmerco_config_t), POINTER(c_void_p)]),
+    "kmerco_destroy": (None, [c_void_p]),
+    "kmerco_insert": (c_int, [c_void_p, c_void_p, c_void_p, c_uint64]),
+    "kmerco_classify": (c_int, [c_void_p]),
+    "kmerco_stats": (c_int, [c_void_p, POINTER(kmerco_stats_t)]),
+    "kmerco_get_counters": (c_int, [c_void_p, c_void_p, c_uint64]),
+    "kmerco_get_distinct": (c_int, [c_void_p, c_void_p, c_void_p, c_uint64, _u64p]),
+    "kmerco_get_trusted": (c_int, [c_void_p, c_void_p, c_uint64, _u64p]),
+    "kmerco_get_erroneous": (c_int, [c_void_p, c_void_p, c_uint64, _u64p]),
+    "kmerco_query": (c_int, [c_void_p, c_void_p, c_uint64, c_void_p]),
+    "kmerco_merge": (c_int, [c_void_p, c_void_p]),
+    "kmerco_reset": (c_int, [c_void_p]),
+    "kmerco_strerror": (c_char_p, [c_int]),
+}
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load libkmerco.so, compiling it first when it is missing or stale."""
+    global _lib
+    if _lib is None:
+        if build:
+            from . import build as _build
+            try:
+                _build.build()
+            except Exception:
+                if not os.path.exists(LIB_PATH):
+                    raise
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"countBF CUDA library not found at {LIB_PATH}")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, call: str) -> None:
+    if status != OK:
+        raise KmercoError(status, call)
+
+
+def _ptr(x) -> int | None:
+    """Address of a numpy array, a torch tensor (host or device) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot pass {type(x).__name__} as a pointer")
+
+
+# --------------------------------------------------------------- C-named calls
+def kmerco_strerror(status: int) -> str:
+    return load().kmerco_strerror(status).decode()
+
+
+def kmerco_create(k: int, m: int, counter_bits: int, nhash: int, threshold: int) -> int:
+    h = c_void_p()
+    _check(load().kmerco_create(k, m, counter_bits, nhash, threshold, byref(h)), "kmerco_create")
+    return h.value
+
+
+def kmerco_create_ex(k: int, m: int, counter_bits: int, nhash: int, threshold: int,
+                     forward_only: bool = False, stream: int | None = None,
+                     hbm_budget: int = 0, device: int = -1) -> int:
+    cfg = kmerco_config_t(k, m, counter_bits, nhash, threshold, int(forward_only),
+                          stream or None, hbm_budget, device)
+    h = c_void_p()
+    _check(load().kmerco_create_ex(byref(cfg), byref(h)), "kmerco_create_ex")
+    return h.value
+
+
+def kmerco_destroy(h: int) -> None:
+    load().kmerco_destroy(h)
+
+
+def kmerco_insert(h: int, bases, offsets, nreads: int | None = None) -> None:
+    if nreads is None:
+        nreads = len(offsets) - 1
+    _check(load().kmerco_insert(h, _ptr(bases), _ptr(offsets), nreads), "kmerco_insert")
+
+
+def kmerco_classify(h: int) -> None:
+    _check(load().kmerco_classify(h), "kmerco_classify")
+
+
+def kmerco_stats(h: int) -> dict:
+    s = kmerco_stats_t()
+    _check(load().kmerco_stats(h, byref(s)), "kmerco_stats")
+    return s.as_dict()
+
+
+def kmerco_get_counters(h: int, dst, nwords: int) -> None:
+    _check(load().kmerco_get_counters(h, _ptr(dst), nwords), "kmerco_get_counters")
+
+
+def kmerco_get_distinct(h: int, keys=None, est=None, cap: int = 0) -> int:
+    n = c_uint64(0)
+    _check(load().kmerco_get_distinct(h, _ptr(keys), _ptr(est), cap, byref(n)),
+           "kmerco_get_distinct")
+    return n.value
+
+
+def kmerco_get_trusted(h: int, keys=None, cap: int = 0) -> int:
+    n = c_uint64(0)
+    _check(load().kmerco_get_trusted(h, _ptr(keys), cap, byref(n)), "kmerco_get_trusted")
+    return n.value
+
+
+def kmerco_get_erroneous(h: int, keys=None, cap: int = 0) -> int:
+    n = c_uint64(0)
+    _check(load().kmerco_get_erroneous(h, _ptr(keys), cap, byref(n)), "kmerco_get_erroneous")
+    return n.value
+
+
+def kmerco_query(h: int, keys, n: int, est) -> None:
+    _check(load().kmerco_query(h, _ptr(keys), n, _ptr(est)), "kmerco_query")
+
+
+def kmerco_merge(dst: int, src: int) -> None:
+    _check(load().kmerco_merge(dst, src), "kmerco_merge")
+
+
+def kmerco_reset(h: int) -> None:
+    _check(load().kmerco_reset(h), "kmerco_reset")
+
+
+# ------------------------------------------------------------------ wrapper
+class CountBF:
+    """One countBF handle with numpy results.
+
+    Keys come back as ``uint64`` arrays: shape ``(n,)`` for K <= 32, shape
+    ``(n, 2)`` holding ``[lo, hi]`` words for 33 <= K <= 64.
+    """
+
+    def __init__(self, k: int, m: int, counter_bits: int = 4, nhash: int = 4,
+                 threshold: int = 3, forward_only: bool = False, stream: int | None = None,
+                 hbm_budget: int = 0, device: int = -1):
+        self.k = k
+        self.kw = 1 if k <= 32 else 2
+        self.h = kmerco_create_ex(k, m, counter_bits, nhash, threshold, forward_only, stream,
+                                  hbm_budget, device)
+
+    def close(self) -> None:
+        if self.h:
+            kmerco_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def insert(self, bases, offsets) -> None:
+        kmerco_insert(self.h, bases, offsets, len(offsets) - 1)
+
+    def classify(self) -> None:
+        kmerco_classify(self.h)
+
+    def reset(self) -> None:
+        kmerco_reset(self.h)
+
+    def stats(self) -> dict:
+        return kmerco_stats(self.h)
+
+    def counters(self) -> np.ndarray:
+        w = self.stats()["words"]
+        out = np.zeros(w, np.uint64)
+        kmerco_get_counters(self.h, out, w)
+        return out
+
+    def _shape(self, n: int) -> tuple:
+        return (n,) if self.kw == 1 else (n, 2)
+
+    def distinct(self) -> tuple[np.ndarray, np.ndarray]:
+        n = kmerco_get_distinct(self.h)
+        keys = np.zeros(self._shape(max(n, 1)), np.uint64)
+        est = np.zeros(max(n, 1), np.uint32)
+        kmerco_get_distinct(self.h, keys, est, n)
+        return keys[:n], est[:n]
+
+    def trusted(self) -> np.ndarray:
+        n = kmerco_get_trusted(self.h)
+        keys = np.zeros(self._shape(max(n, 1)), np.uint64)
+        kmerco_get_trusted(self.h, keys, n)
+        return keys[:n]
+
+    def erroneous(self) -> np.ndarray:
+        n = kmerco_get_erroneous(self.h)
+        keys = np.zeros(self._shape(max(n, 1)), np.uint64)
+        kmerco_get_erroneous(self.h, keys, n)
+        return keys[:n]
+
+    def query(self, keys: np.ndarray) -> np.ndarray:
+        keys = np.ascontiguousarray(keys, np.uint64)
+        n = keys.shape[0]
+        est = np.zeros(max(n, 1), np.uint32)
+        kmerco_query(self.h, keys, n, est)
+        return est[:n]
+
+    def merge(self, other: "CountBF") -> None:
+        kmerco_merge(self.h, other.h)

@@ -1,0 +1,605 @@
+// Host side of the countBF C ABI (include/kmerco.h): argument validation,
+// device memory, pointer-kind detection, capacity management of the
+// distinct-key set, and the order of kernel launches for each phase.
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include <cuda_runtime.h>
+
+#include "../../include/kmerco.h"
+#include "kmerco_internal.cuh"
+
+using namespace countbf;
+
+struct kmerco {
+    int K, kw, alpha, eta, nhash, canonical;
+    uint32_t tau;
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    int insert_grid;
+    uint64_t budget, used;
+    Geometry G;
+    DevCounters *ctr;        // device
+    DevCounters *ctr_host;   // pinned mirror
+    uint64_t *table;         // distinct-key set: cap slots of kw words
+    uint64_t cap;
+    uint64_t *dlist;         // distinct keys in arrival order
+    uint64_t dlist_cap;
+    uint64_t d_ub;           // upper bound of the distinct keys held
+    uint8_t *in_bases;       // staging of host inputs
+    uint64_t in_bases_cap;
+    uint64_t *in_offsets;
+    uint64_t in_offsets_cap;
+    uint32_t *first_read;
+    uint64_t first_read_cap;
+    uint64_t *alt0, *alt1;   // radix-sort buffers
+    uint64_t alt0_cap, alt1_cap;
+    uint32_t *est;
+    uint64_t est_cap;
+    uint64_t *split;         // trusted keys then erroneous keys
+    uint64_t split_cap;
+    uint32_t *sort_scratch;
+    uint64_t sort_scratch_cap;
+    uint64_t *split_scratch;
+    uint64_t split_scratch_cap;
+    uint64_t *q_keys;        // staging of kmerco_query
+    uint32_t *q_est;
+    uint64_t q_cap;
+    const uint64_t *sorted;  // sorted distinct keys (one of dlist, alt0, alt1)
+    uint64_t n_distinct, n_trusted;
+    bool classified;
+    cudaEvent_t ev[4];
+    bool insert_timed, classify_timed;
+    uint64_t launches;       // kernels launched by this handle
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1, want;
+    explicit DeviceGuard(int d) : want(d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != want) cudaSetDevice(want);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0 && prev != want) cudaSetDevice(prev);
+    }
+};
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return KMERCO_OK;
+    return e == cudaErrorMemoryAllocation ? KMERCO_ENOMEM : KMERCO_ECUDA;
+}
+
+#define KM_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_status(e_); \
+    } while (0)
+#define KM_TRY(call)                     \
+    do {                                 \
+        int r_ = (call);                 \
+        if (r_ != KMERCO_OK) return r_;  \
+    } while (0)
+
+int dev_alloc(kmerco_t *h, void **p, uint64_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (h->budget && h->used + bytes > h->budget) return KMERCO_ENOMEM;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return KMERCO_ENOMEM;
+    }
+    h->used += bytes;
+    return KMERCO_OK;
+}
+
+void dev_free(kmerco_t *h, void *p, uint64_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    h->used -= bytes ? bytes : 16;
+}
+
+// Make *p hold at least `need` elements of `elem` bytes (contents dropped).
+template <typename T>
+int ensure(kmerco_t *h, T **p, uint64_t *cap, uint64_t need, uint64_t elem = sizeof(T)) {
+    if (*p && *cap >= need) return KMERCO_OK;
+    uint64_t want = need + need / 4 + 64;
+    dev_free(h, *p, *cap * elem);
+    *p = nullptr;
+    *cap = 0;
+    void *q;
+    KM_TRY(dev_alloc(h, &q, want * elem));
+    *p = (T *)q;
+    *cap = want;
+    return KMERCO_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int read_counters(kmerco_t *h) {
+    KM_CUDA(cudaMemcpyAsync(h->ctr_host, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                            h->stream));
+    KM_CUDA(cudaStreamSynchronize(h->stream));
+    return KMERCO_OK;
+}
+
+int device_error_status(unsigned err) {
+    if (err & kErrListFull) return KMERCO_ENOMEM;
+    if (err & (kErrCasLimit | kErrProbeLimit)) return KMERCO_ETIMEOUT;
+    return KMERCO_OK;
+}
+
+// The distinct-key set must keep its load factor at or below 1/2 for every
+// key the next launch could add: cap >= 2 * (distinct so far + new windows).
+int ensure_set_capacity(kmerco_t *h, uint64_t add) {
+    uint64_t need = h->d_ub + add;
+    if (need <= h->dlist_cap && 2 * need <= h->cap) {
+        h->d_ub = need;
+        return KMERCO_OK;
+    }
+    KM_TRY(read_counters(h));
+    const uint64_t D = h->ctr_host->distinct;
+    need = D + add;
+    if (need > h->dlist_cap) {
+        uint64_t want = need > h->dlist_cap + h->dlist_cap / 2 ? need : h->dlist_cap + h->dlist_cap / 2;
+        void *q;
+        KM_TRY(dev_alloc(h, &q, want * h->kw * 8));
+        if (D) KM_CUDA(cudaMemcpyAsync(q, h->dlist, D * h->kw * 8, cudaMemcpyDeviceToDevice, h->stream));
+        KM_CUDA(cudaStreamSynchronize(h->stream));
+        dev_free(h, h->dlist, h->dlist_cap * h->kw * 8);
+        h->dlist = (uint64_t *)q;
+        h->dlist_cap = want;
+    }
+    if (2 * need > h->cap) {
+        uint64_t want = 2 * need;
+        if (want < h->cap + h->cap / 2) want = h->cap + h->cap / 2;
+        if (want < 1024) want = 1024;
+        void *q;
+        KM_TRY(dev_alloc(h, &q, want * h->kw * 8));
+        KM_CUDA(cudaMemsetAsync(q, 0xFF, want * h->kw * 8, h->stream));
+        KM_CUDA(launch_reinsert(h->dlist, D, h->kw, (uint64_t *)q, want, nullptr, 0, h->ctr,
+                                h->stream));
+        h->launches += D ? 1 : 0;
+        KM_CUDA(cudaStreamSynchronize(h->stream));
+        dev_free(h, h->table, h->cap * h->kw * 8);
+        h->table = (uint64_t *)q;
+        h->cap = want;
+    }
+    h->d_ub = need;
+    return KMERCO_OK;
+}
+
+int validate(const kmerco_config_t *c) {
+    if (!c) return KMERCO_EINVAL;
+    if (c->k < 1 || c->k > 64) return KMERCO_EINVAL;
+    if (c->counter_bits < 1 || c->counter_bits > 32) return KMERCO_EINVAL;
+    if (c->nhash < 1 || c->nhash > 32) return KMERCO_EINVAL;
+    if (c->m < 1 || c->m > (1ull << 48)) return KMERCO_EINVAL;
+    const uint64_t maxc = (1ull << c->counter_bits) - 1;
+    if ((uint64_t)c->threshold >= maxc) return KMERCO_EINVAL;
+    if (c->forward_only != 0 && c->forward_only != 1) return KMERCO_EINVAL;
+    return KMERCO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kmerco_strerror(int status) {
+    switch (status) {
+    case KMERCO_OK: return "ok";
+    case KMERCO_EINVAL: return "invalid argument";
+    case KMERCO_ENOMEM: return "out of device memory or over the HBM budget";
+    case KMERCO_ECUDA: return "CUDA error";
+    case KMERCO_ETIMEOUT: return "a bounded device retry loop gave up";
+    case KMERCO_ESTATE: return "call not valid in the current state";
+    case KMERCO_ESIZE: return "buffer too small";
+    default: return "unknown status";
+    }
+}
+
+int kmerco_create(int k, uint64_t m, int counter_bits, int nhash, uint32_t threshold,
+                  kmerco_t **out) {
+    kmerco_config_t c;
+    memset(&c, 0, sizeof(c));
+    c.k = k;
+    c.m = m;
+    c.counter_bits = counter_bits;
+    c.nhash = nhash;
+    c.threshold = threshold;
+    c.device = -1;
+    return kmerco_create_ex(&c, out);
+}
+
+int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
+    if (!out) return KMERCO_EINVAL;
+    *out = nullptr;
+    KM_TRY(validate(cfg));
+    kmerco_t *h = new (std::nothrow) kmerco_t;
+    if (!h) return KMERCO_ENOMEM;
+    memset(h, 0, sizeof(*h));
+    h->K = cfg->k;
+    h->kw = cfg->k <= 32 ? 1 : 2;
+    h->alpha = cfg->counter_bits;
+    h->eta = 64 / cfg->counter_bits;
+    h->nhash = cfg->nhash;
+    h->tau = cfg->threshold;
+    h->canonical = cfg->forward_only ? 0 : 1;
+    h->budget = cfg->hbm_budget;
+    if (cfg->device >= 0) {
+        h->device = cfg->device;
+    } else if (cudaGetDevice(&h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return KMERCO_ECUDA;
+    }
+    DeviceGuard guard(h->device);
+    int status = KMERCO_OK;
+    do {
+        if (cfg->stream) {
+            h->stream = (cudaStream_t)cfg->stream;
+        } else {
+            if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+                status = KMERCO_ECUDA;
+                break;
+            }
+            h->own_stream = true;
+        }
+        for (int i = 0; i < 4; ++i)
+            if (cudaEventCreate(&h->ev[i]) != cudaSuccess) status = KMERCO_ECUDA;
+        if (status) break;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        h->insert_grid = (sms > 0 ? sms : 1) * insert_blocks_per_sm();
+
+        const uint64_t eta = (uint64_t)h->eta;
+        Geometry &G = h->G;
+        G.alpha = h->alpha;
+        G.eta = h->eta;
+        G.nhash = h->nhash;
+        G.words = (cfg->m + eta - 1) / eta;
+        G.m = G.words * eta;
+        G.m_mask = (G.m & (G.m - 1)) == 0 ? G.m - 1 : 0;
+        G.maxc = (1ull << h->alpha) - 1;
+        G.eta_log2 = -1;
+        for (int b = 0; b < 7; ++b)
+            if ((1 << b) == h->eta) G.eta_log2 = b;
+        void *p;
+        if ((status = dev_alloc(h, &p, G.words * 8))) break;
+        G.cells = (uint64_t *)p;
+        if ((status = dev_alloc(h, &p, sizeof(DevCounters)))) break;
+        h->ctr = (DevCounters *)p;
+        if (cudaMallocHost((void **)&h->ctr_host, sizeof(DevCounters)) != cudaSuccess) {
+            status = KMERCO_ENOMEM;
+            break;
+        }
+        memset(h->ctr_host, 0, sizeof(DevCounters));
+        if (cudaMemsetAsync(G.cells, 0, G.words * 8, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            status = KMERCO_ECUDA;
+            break;
+        }
+    } while (0);
+    if (status) {
+        cudaGetLastError();
+        kmerco_destroy(h);
+        return status;
+    }
+    *out = h;
+    return KMERCO_OK;
+}
+
+void kmerco_destroy(kmerco_t *h) {
+    if (!h) return;
+    {
+        DeviceGuard guard(h->device);
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        dev_free(h, h->G.cells, h->G.words * 8);
+        dev_free(h, h->ctr, sizeof(DevCounters));
+        dev_free(h, h->table, h->cap * h->kw * 8);
+        dev_free(h, h->dlist, h->dlist_cap * h->kw * 8);
+        dev_free(h, h->in_bases, h->in_bases_cap);
+        dev_free(h, h->in_offsets, h->in_offsets_cap * 8);
+        dev_free(h, h->first_read, h->first_read_cap * 4);
+        dev_free(h, h->alt0, h->alt0_cap * 8);
+        dev_free(h, h->alt1, h->alt1_cap * 8);
+        dev_free(h, h->est, h->est_cap * 4);
+        dev_free(h, h->split, h->split_cap * 8);
+        dev_free(h, h->sort_scratch, h->sort_scratch_cap * 4);
+        dev_free(h, h->split_scratch, h->split_scratch_cap * 8);
+        dev_free(h, h->q_keys, h->q_cap * 16);
+        dev_free(h, h->q_est, h->q_cap * 4);
+        if (h->ctr_host) cudaFreeHost(h->ctr_host);
+        for (int i = 0; i < 4; ++i)
+            if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        cudaGetLastError();
+    }
+    delete h;
+}
+
+int kmerco_reset(kmerco_t *h) {
+    if (!h) return KMERCO_EINVAL;
+    DeviceGuard guard(h->device);
+    KM_CUDA(cudaMemsetAsync(h->G.cells, 0, h->G.words * 8, h->stream));
+    if (h->table && h->d_ub) KM_CUDA(cudaMemsetAsync(h->table, 0xFF, h->cap * h->kw * 8, h->stream));
+    KM_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->stream));
+    h->d_ub = 0;
+    h->classified = false;
+    h->n_distinct = h->n_trusted = 0;
+    h->insert_timed = h->classify_timed = false;
+    return KMERCO_OK;
+}
+
+int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint64_t nreads) {
+    if (!h) return KMERCO_EINVAL;
+    if (nreads == 0) return KMERCO_OK;
+    if (!offsets || nreads >= 0xFFFFFFFFull) return KMERCO_EINVAL;
+    DeviceGuard guard(h->device);
+    const int K = h->K;
+    uint64_t first, last, bound = 0;
+    const uint64_t *d_off;
+    if (!is_device_ptr(offsets)) {
+        first = offsets[0];
+        last = offsets[nreads];
+        for (uint64_t r = 0; r < nreads; ++r) {
+            const uint64_t s = offsets[r], e = offsets[r + 1];
+            if (e < s) return KMERCO_EINVAL;
+            if (e - s >= (uint64_t)K) bound += e - s - K + 1;
+        }
+        KM_TRY(ensure(h, &h->in_offsets, &h->in_offsets_cap, nreads + 1));
+        KM_CUDA(cudaMemcpyAsync(h->in_offsets, offsets, (nreads + 1) * 8, cudaMemcpyHostToDevice,
+                                h->stream));
+        d_off = h->in_offsets;
+    } else {
+        KM_CUDA(cudaMemsetAsync(&h->ctr->bound, 0, sizeof(h->ctr->bound), h->stream));
+        KM_CUDA(cudaMemsetAsync(&h->ctr->bad_offsets, 0, sizeof(h->ctr->bad_offsets), h->stream));
+        KM_CUDA(launch_window_bound(offsets, nreads, K, h->ctr, h->stream));
+        h->launches += 1;
+        KM_TRY(read_counters(h));
+        if (h->ctr_host->bad_offsets) return KMERCO_EINVAL;
+        first = h->ctr_host->first;
+        last = h->ctr_host->last;
+        bound = h->ctr_host->bound;
+        d_off = offsets;
+    }
+    const uint64_t nbytes = last - first;
+    if (nbytes && !bases) return KMERCO_EINVAL;
+    const uint8_t *d_bases = nullptr;
+    if (nbytes) {
+        if (is_device_ptr(bases)) {
+            d_bases = (const uint8_t *)bases + first;
+        } else {
+            KM_TRY(ensure(h, &h->in_bases, &h->in_bases_cap, nbytes));
+            KM_CUDA(cudaMemcpyAsync(h->in_bases, bases + first, nbytes, cudaMemcpyHostToDevice,
+                                    h->stream));
+            d_bases = h->in_bases;
+        }
+    }
+    if (bound == 0) return KMERCO_OK;   // no window fits in any read
+    KM_TRY(ensure_set_capacity(h, bound));
+    const uint64_t nchunks = (nbytes + kChunk - 1) / kChunk;
+    KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, nchunks));
+    KM_CUDA(launch_first_read(d_off, nreads, first, nchunks, h->first_read, h->stream));
+    h->launches += nchunks ? 1 : 0;
+
+    InsertArgs a;
+    a.bases = d_bases;
+    a.offsets = d_off;
+    a.nreads = nreads;
+    a.first = first;
+    a.last = last;
+    a.first_read = h->first_read;
+    a.nchunks = nchunks;
+    a.K = K;
+    a.canonical = h->canonical;
+    a.G = h->G;
+    a.table = h->table;
+    a.cap = h->cap;
+    a.dlist = h->dlist;
+    a.dlist_cap = h->dlist_cap;
+    a.ctr = h->ctr;
+    KM_CUDA(cudaEventRecord(h->ev[0], h->stream));
+    KM_CUDA(launch_insert(a, h->insert_grid, h->stream));
+    h->launches += nchunks ? 1 : 0;
+    KM_CUDA(cudaEventRecord(h->ev[1], h->stream));
+    h->insert_timed = true;
+    h->classified = false;
+    return KMERCO_OK;
+}
+
+int kmerco_classify(kmerco_t *h) {
+    if (!h) return KMERCO_EINVAL;
+    if (h->classified) return KMERCO_OK;
+    DeviceGuard guard(h->device);
+    KM_TRY(read_counters(h));
+    KM_TRY(device_error_status(h->ctr_host->error));
+    const uint64_t D = h->ctr_host->distinct;
+    if (D >= 0xFFFFFFFFull) return KMERCO_ENOMEM;   // radix tiles index keys with 32 bits
+    const int kw = h->kw;
+    KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, D * kw));
+    KM_TRY(ensure(h, &h->alt1, &h->alt1_cap, D * kw));
+    KM_TRY(ensure(h, &h->est, &h->est_cap, D));
+    KM_TRY(ensure(h, &h->split, &h->split_cap, D * kw));
+    KM_TRY(ensure(h, &h->sort_scratch, &h->sort_scratch_cap, sort_scratch_words(D, kw)));
+    KM_TRY(ensure(h, &h->split_scratch, &h->split_scratch_cap, split_scratch_words(D)));
+    KM_CUDA(cudaEventRecord(h->ev[2], h->stream));
+    const uint64_t *sorted = h->dlist;
+    KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D, kw, 2 * h->K, h->sort_scratch, &sorted,
+                       h->stream));
+    KM_CUDA(launch_query(sorted, D, kw, h->K, h->G, h->est, h->stream));
+    KM_CUDA(launch_split(sorted, h->est, D, kw, h->tau, h->split, h->split_scratch, h->ctr,
+                         h->stream));
+    if (D > 1) h->launches += 3 * (uint64_t)((2 * h->K + kRadixBits - 1) / kRadixBits);
+    if (D > 0) h->launches += 4;   // query + three split kernels
+    KM_CUDA(cudaEventRecord(h->ev[3], h->stream));
+    KM_TRY(read_counters(h));
+    h->sorted = sorted;
+    h->n_distinct = D;
+    h->n_trusted = h->ctr_host->trusted;
+    h->classified = true;
+    h->classify_timed = true;
+    return KMERCO_OK;
+}
+
+int kmerco_stats(kmerco_t *h, kmerco_stats_t *s) {
+    if (!h || !s) return KMERCO_EINVAL;
+    DeviceGuard guard(h->device);
+    KM_CUDA(launch_count_saturated(h->G, h->ctr, h->stream));
+    h->launches += 1;
+    KM_TRY(read_counters(h));
+    memset(s, 0, sizeof(*s));
+    const DevCounters &c = *h->ctr_host;
+    s->windows = c.windows;
+    s->n_skipped = c.skipped;
+    s->inserted = c.inserted;
+    s->distinct = c.distinct;
+    if (h->classified) {
+        s->trustworthy = h->n_trusted;
+        s->erroneous = h->n_distinct - h->n_trusted;
+    }
+    s->saturated_counters = c.saturated;
+    s->m_actual = h->G.m;
+    s->words = h->G.words;
+    s->device_bytes = h->used;
+    s->launches = h->launches;
+    s->k = h->K;
+    s->counter_bits = h->alpha;
+    s->eta = h->eta;
+    s->nhash = h->nhash;
+    s->threshold = h->tau;
+    s->classified = h->classified ? 1 : 0;
+    if (h->insert_timed) cudaEventElapsedTime(&s->insert_ms, h->ev[0], h->ev[1]);
+    if (h->classify_timed) cudaEventElapsedTime(&s->classify_ms, h->ev[2], h->ev[3]);
+    cudaGetLastError();
+    return device_error_status(c.error);
+}
+
+static int copy_out(kmerco_t *h, void *dst, const void *src, uint64_t bytes) {
+    if (bytes == 0) return KMERCO_OK;
+    KM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
+    KM_CUDA(cudaStreamSynchronize(h->stream));
+    return KMERCO_OK;
+}
+
+int kmerco_get_counters(kmerco_t *h, uint64_t *dst, uint64_t nwords) {
+    if (!h || !dst) return KMERCO_EINVAL;
+    if (nwords < h->G.words) return KMERCO_ESIZE;
+    DeviceGuard guard(h->device);
+    return copy_out(h, dst, h->G.cells, h->G.words * 8);
+}
+
+int kmerco_get_distinct(kmerco_t *h, uint64_t *keys, uint32_t *est, uint64_t cap, uint64_t *n) {
+    if (!h || !n) return KMERCO_EINVAL;
+    if (!h->classified) return KMERCO_ESTATE;
+    *n = h->n_distinct;
+    if (!keys) return KMERCO_OK;
+    if (cap < h->n_distinct) return KMERCO_ESIZE;
+    DeviceGuard guard(h->device);
+    KM_TRY(copy_out(h, keys, h->sorted, h->n_distinct * h->kw * 8));
+    if (est) KM_TRY(copy_out(h, est, h->est, h->n_distinct * 4));
+    return KMERCO_OK;
+}
+
+int kmerco_get_trusted(kmerco_t *h, uint64_t *keys, uint64_t cap, uint64_t *n) {
+    if (!h || !n) return KMERCO_EINVAL;
+    if (!h->classified) return KMERCO_ESTATE;
+    *n = h->n_trusted;
+    if (!keys) return KMERCO_OK;
+    if (cap < h->n_trusted) return KMERCO_ESIZE;
+    DeviceGuard guard(h->device);
+    return copy_out(h, keys, h->split, h->n_trusted * h->kw * 8);
+}
+
+int kmerco_get_erroneous(kmerco_t *h, uint64_t *keys, uint64_t cap, uint64_t *n) {
+    if (!h || !n) return KMERCO_EINVAL;
+    if (!h->classified) return KMERCO_ESTATE;
+    const uint64_t E = h->n_distinct - h->n_trusted;
+    *n = E;
+    if (!keys) return KMERCO_OK;
+    if (cap < E) return KMERCO_ESIZE;
+    DeviceGuard guard(h->device);
+    return copy_out(h, keys, h->split + h->n_trusted * h->kw, E * h->kw * 8);
+}
+
+int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est) {
+    if (!h) return KMERCO_EINVAL;
+    if (n == 0) return KMERCO_OK;
+    if (!keys || !est) return KMERCO_EINVAL;
+    DeviceGuard guard(h->device);
+    const int kw = h->kw;
+    const uint64_t *dk = keys;
+    uint32_t *de = est;
+    const bool keys_dev = is_device_ptr(keys), est_dev = is_device_ptr(est);
+    if (!keys_dev || !est_dev) {
+        if (!h->q_keys || h->q_cap < n) {
+            dev_free(h, h->q_keys, h->q_cap * 16);
+            dev_free(h, h->q_est, h->q_cap * 4);
+            h->q_keys = nullptr;
+            h->q_est = nullptr;
+            h->q_cap = 0;
+            void *p;
+            KM_TRY(dev_alloc(h, &p, n * 16));
+            h->q_keys = (uint64_t *)p;
+            if (dev_alloc(h, &p, n * 4) != KMERCO_OK) {
+                dev_free(h, h->q_keys, n * 16);
+                h->q_keys = nullptr;
+                return KMERCO_ENOMEM;
+            }
+            h->q_est = (uint32_t *)p;
+            h->q_cap = n;
+        }
+    }
+    if (!keys_dev) {
+        KM_CUDA(cudaMemcpyAsync(h->q_keys, keys, n * kw * 8, cudaMemcpyHostToDevice, h->stream));
+        dk = h->q_keys;
+    }
+    if (!est_dev) de = h->q_est;
+    KM_CUDA(launch_query(dk, n, kw, h->K, h->G, de, h->stream));
+    h->launches += 1;
+    if (!est_dev) KM_CUDA(cudaMemcpyAsync(est, de, n * 4, cudaMemcpyDeviceToHost, h->stream));
+    KM_CUDA(cudaStreamSynchronize(h->stream));
+    return KMERCO_OK;
+}
+
+int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
+    if (!dst || !src || dst == src) return KMERCO_EINVAL;
+    if (dst->K != src->K || dst->G.m != src->G.m || dst->alpha != src->alpha ||
+        dst->nhash != src->nhash || dst->canonical != src->canonical || dst->device != src->device)
+        return KMERCO_EINVAL;
+    DeviceGuard guard(dst->device);
+    KM_TRY(read_counters(src));
+    KM_TRY(device_error_status(src->ctr_host->error));
+    const DevCounters sc = *src->ctr_host;
+    KM_TRY(ensure_set_capacity(dst, sc.distinct));
+    KM_CUDA(launch_merge(dst->G.cells, src->G.cells, dst->G, dst->stream));
+    KM_CUDA(launch_reinsert(src->dlist, sc.distinct, dst->kw, dst->table, dst->cap, dst->dlist,
+                            dst->dlist_cap, dst->ctr, dst->stream));
+    dst->launches += sc.distinct ? 2 : 1;
+    KM_TRY(read_counters(dst));
+    DevCounters dc = *dst->ctr_host;
+    dc.windows += sc.windows;
+    dc.skipped += sc.skipped;
+    dc.inserted += sc.inserted;
+    // only the three totals change; the device may not touch them meanwhile
+    KM_CUDA(cudaMemcpyAsync(&dst->ctr->windows, &dc.windows, 3 * sizeof(unsigned long long),
+                            cudaMemcpyHostToDevice, dst->stream));
+    KM_CUDA(cudaStreamSynchronize(dst->stream));
+    dst->classified = false;
+    return KMERCO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,390 @@
+// Classification phase of KmerCo (Algorithm 2 with QcountBF-II, Algorithm 5)
+// and the countBF merge, on sm_103a.
+//
+//  - radix_sort: least-significant-digit radix sort of the distinct keys
+//    (8-bit digits, only the 2K bits a key can use).  Per pass: per-tile
+//    digit counts, one scan per digit across tiles, then a stable scatter
+//    in which each warp ranks equal digits with __match_any_sync and the
+//    tile is reordered in shared memory before coalesced stores.
+//  - query: per key, k_h hashes and the minimum counter, 0 if any is 0.
+//  - split: stable partition on est > tau (trustworthy first).
+//  - merge: counter-wise min(a + b, 2^alpha - 1) of two countBFs.
+#include "kmerco_internal.cuh"
+
+namespace countbf {
+namespace {
+
+constexpr int kWarps = kSortThreads / 32;
+
+// Exclusive scan across a 256-thread block; `total` receives the block sum.
+template <typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T &total) {
+    __shared__ T warp_sums[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T s = lane < kWarps ? warp_sums[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < kWarps; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < kWarps) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    T before = warp ? warp_sums[warp - 1] : T(0);
+    total = warp_sums[kWarps - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+template <int KW>
+__device__ __forceinline__ unsigned digit_of(const uint64_t *k, int shift) {
+    if (KW == 1 || shift < 64) return (unsigned)(k[0] >> shift) & (kRadixBins - 1);
+    return (unsigned)(k[1] >> (shift - 64)) & (kRadixBins - 1);
+}
+
+template <int KW>
+__host__ __device__ constexpr int tile_keys() { return kSortThreads * (kSortItems / KW); }
+
+// counts[d * ntiles + tile] = keys of the tile with digit d.
+template <int KW>
+__global__ void __launch_bounds__(kSortThreads) upsweep_kernel(const uint64_t *in, uint64_t n,
+                                                               int shift, uint32_t *counts,
+                                                               uint32_t ntiles) {
+    __shared__ unsigned hist[kRadixBins];
+    const int tid = threadIdx.x;
+    hist[tid] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * tile_keys<KW>();
+#pragma unroll 4
+    for (int j = 0; j < kSortItems / KW; ++j) {
+        uint64_t idx = base + (uint64_t)j * kSortThreads + tid;
+        if (idx < n) atomicAdd(&hist[digit_of<KW>(in + idx * KW, shift)], 1u);
+    }
+    __syncthreads();
+    counts[(uint64_t)tid * ntiles + blockIdx.x] = hist[tid];
+}
+
+// Row d of counts becomes its exclusive prefix over tiles; totals[d] = row sum.
+__global__ void __launch_bounds__(kSortThreads) scan_rows_kernel(uint32_t *counts, uint32_t ntiles,
+                                                                 uint32_t *totals) {
+    uint32_t *row = counts + (uint64_t)blockIdx.x * ntiles;
+    uint32_t carry = 0;
+    for (uint32_t s0 = 0; s0 < ntiles; s0 += kSortThreads * 4) {
+        uint32_t v[4], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t idx = s0 + threadIdx.x * 4 + j;
+            v[j] = idx < ntiles ? row[idx] : 0u;
+            sum += v[j];
+        }
+        uint32_t tot;
+        uint32_t pre = block_exclusive_scan<uint32_t>(sum, tot) + carry;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t idx = s0 + threadIdx.x * 4 + j;
+            if (idx < ntiles) row[idx] = pre;
+            pre += v[j];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint64_t *in, uint64_t *out,
+                                                                 uint64_t n, int shift,
+                                                                 const uint32_t *counts,
+                                                                 const uint32_t *totals,
+                                                                 uint32_t ntiles) {
+    constexpr int ITEMS = kSortItems / KW;
+    constexpr int TILE = tile_keys<KW>();
+    __shared__ uint32_t wcnt[kWarps][kRadixBins];
+    __shared__ uint32_t tstart[kRadixBins];
+    __shared__ uint64_t gofs[kRadixBins];
+    __shared__ uint64_t stage[TILE * KW];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t tile_base = (uint64_t)blockIdx.x * TILE;
+    for (int d = lane; d < kRadixBins; d += 32) wcnt[warp][d] = 0;
+
+    uint64_t key[ITEMS][KW];
+    unsigned dig[ITEMS], rank[ITEMS];
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        uint64_t idx = tile_base + (uint64_t)warp * (32 * ITEMS) + j * 32 + lane;
+        if (idx < n) {
+#pragma unroll
+            for (int w = 0; w < KW; ++w) key[j][w] = in[idx * KW + w];
+            dig[j] = digit_of<KW>(key[j], shift);
+        } else {
+#pragma unroll
+            for (int w = 0; w < KW; ++w) key[j][w] = 0;
+            dig[j] = kRadixBins - 1;   // past the end: ranked last, never stored
+        }
+    }
+    __syncwarp();
+    // stable rank within the warp: items in (j, lane) order
+    const unsigned lt = (1u << lane) - 1;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
+        const unsigned prev = wcnt[warp][dig[j]];
+        __syncwarp();
+        if (lane == __ffs(peers) - 1) wcnt[warp][dig[j]] = prev + __popc(peers);
+        __syncwarp();
+        rank[j] = prev + __popc(peers & lt);
+    }
+    __syncthreads();
+
+    // per digit: offsets of each warp within the tile, tile start of the digit
+    {
+        const int d = tid;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            uint32_t c = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += c;
+        }
+        uint32_t tot;
+        tstart[d] = block_exclusive_scan<uint32_t>(run, tot);
+        uint64_t t64 = totals[d], dtot;
+        uint64_t dbase = block_exclusive_scan<uint64_t>(t64, dtot);
+        gofs[d] = dbase + counts[(uint64_t)d * ntiles + blockIdx.x];
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+        uint64_t idx = tile_base + (uint64_t)warp * (32 * ITEMS) + j * 32 + lane;
+        if (idx < n) {
+            const unsigned pos = tstart[dig[j]] + wcnt[warp][dig[j]] + rank[j];
+#pragma unroll
+            for (int w = 0; w < KW; ++w) stage[pos * KW + w] = key[j][w];
+        }
+    }
+    __syncthreads();
+
+    const uint64_t left = n - tile_base;
+    const unsigned valid = left < (uint64_t)TILE ? (unsigned)left : (unsigned)TILE;
+    for (unsigned i = tid; i < valid; i += kSortThreads) {
+        const unsigned d = digit_of<KW>(stage + i * KW, shift);
+        const uint64_t o = gofs[d] + (i - tstart[d]);
+#pragma unroll
+        for (int w = 0; w < KW; ++w) out[o * KW + w] = stage[i * KW + w];
+    }
+}
+
+// QcountBF-II (Algorithm 5) per key.
+template <int KW>
+__global__ void query_kernel(const uint64_t *keys, uint64_t n, int K, Geometry G, uint32_t *est) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t klo = keys[i * KW];
+        const uint64_t khi = KW == 2 ? keys[i * KW + 1] : 0;
+        const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
+        uint64_t best = ~0ull;
+        for (int a = 0; a < G.nhash; ++a) {
+            uint64_t h1, h2;
+            if (KW == 1)
+                murmur8(k1m, (uint32_t)a, h1, h2);
+            else
+                murmur16(klo, khi, (uint32_t)a, h1, h2);
+            uint64_t cell;
+            unsigned sh;
+            locate(G, counter_of(G, h1), cell, sh);
+            const uint64_t v = (__ldg(G.cells + cell) >> sh) & G.maxc;
+            if (v == 0) {
+                best = 0;
+                break;
+            }
+            best = v < best ? v : best;
+        }
+        est[i] = (uint32_t)best;
+        (void)K;
+    }
+}
+
+// Trusted keys per split tile (each thread owns 16 consecutive keys).
+__global__ void __launch_bounds__(kSortThreads) split_count_kernel(const uint32_t *est, uint64_t n,
+                                                                   uint32_t tau, uint64_t *tile_cnt) {
+    const uint64_t base = (uint64_t)blockIdx.x * kSplitTile + threadIdx.x * 16ull;
+    unsigned c = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) c += (base + j < n) && est[base + j] > tau;
+    unsigned long long tot;
+    block_exclusive_scan<unsigned long long>(c, tot);
+    if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
+}
+
+// Exclusive scan of tile counts in place (one block); total -> ctr->trusted.
+__global__ void __launch_bounds__(kSortThreads) split_scan_kernel(uint64_t *tile_cnt,
+                                                                  uint64_t ntiles, DevCounters *ctr) {
+    unsigned long long carry = 0;
+    for (uint64_t s0 = 0; s0 < ntiles; s0 += kSortThreads) {
+        const uint64_t idx = s0 + threadIdx.x;
+        unsigned long long v = idx < ntiles ? tile_cnt[idx] : 0ull, tot;
+        unsigned long long pre = block_exclusive_scan<unsigned long long>(v, tot) + carry;
+        if (idx < ntiles) tile_cnt[idx] = pre;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) ctr->trusted = carry;
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kSortThreads) split_scatter_kernel(const uint64_t *keys,
+                                                                     const uint32_t *est, uint64_t n,
+                                                                     uint32_t tau,
+                                                                     const uint64_t *tile_pre,
+                                                                     const DevCounters *ctr,
+                                                                     uint64_t *out) {
+    const uint64_t tile0 = (uint64_t)blockIdx.x * kSplitTile;
+    const uint64_t base = tile0 + threadIdx.x * 16ull;
+    unsigned flags = 0, c = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        bool t = (base + j < n) && est[base + j] > tau;
+        flags |= (unsigned)t << j;
+        c += t;
+    }
+    unsigned long long tot;
+    const unsigned long long pre = block_exclusive_scan<unsigned long long>(c, tot);
+    const uint64_t T = ctr->trusted;
+    uint64_t tpos = tile_pre[blockIdx.x] + pre;
+    const uint64_t before = base < n ? base - tile0 : (n > tile0 ? n - tile0 : 0);
+    uint64_t epos = T + (tile0 - tile_pre[blockIdx.x]) + (before - pre);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const uint64_t i = base + j;
+        if (i >= n) break;
+        const uint64_t o = (flags >> j) & 1u ? tpos++ : epos++;
+#pragma unroll
+        for (int w = 0; w < KW; ++w) out[o * KW + w] = keys[i * KW + w];
+    }
+}
+
+// dst = counter-wise min(dst + src, 2^alpha - 1)
+__global__ void merge_kernel(uint64_t *dst, const uint64_t *src, Geometry G) {
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < G.words;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = dst[w], b = src[w];
+        uint64_t r = 0;
+        for (int l = 0; l < G.eta; ++l) {
+            const unsigned sh = (unsigned)(l * G.alpha);
+            uint64_t s = ((a >> sh) & G.maxc) + ((b >> sh) & G.maxc);
+            if (s > G.maxc) s = G.maxc;
+            r |= s << sh;
+        }
+        dst[w] = r;
+    }
+}
+
+__global__ void count_saturated_kernel(Geometry G, DevCounters *ctr) {
+    unsigned long long c = 0;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < G.words;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = G.cells[w];
+        for (int l = 0; l < G.eta; ++l) c += ((v >> (unsigned)(l * G.alpha)) & G.maxc) == G.maxc;
+    }
+    for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->saturated, c);
+}
+
+uint32_t sort_tiles(uint64_t n, int kw) {
+    const uint64_t t = kw == 1 ? (uint64_t)tile_keys<1>() : (uint64_t)tile_keys<2>();
+    return (uint32_t)((n + t - 1) / t);
+}
+
+unsigned grid_for(uint64_t n, unsigned threads, unsigned cap) {
+    uint64_t b = (n + threads - 1) / threads;
+    if (b > cap) b = cap;
+    return b ? (unsigned)b : 1u;
+}
+
+}  // namespace
+
+uint64_t sort_scratch_words(uint64_t n, int kw) {
+    return (uint64_t)kRadixBins * sort_tiles(n, kw) + kRadixBins;
+}
+
+cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint64_t n, int kw,
+                       int bits, uint32_t *counts, const uint64_t **result, cudaStream_t s) {
+    *result = in;
+    if (n <= 1) return cudaSuccess;
+    const uint32_t ntiles = sort_tiles(n, kw);
+    uint32_t *totals = counts + (uint64_t)kRadixBins * ntiles;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    const uint64_t *src = in;
+    for (int p = 0; p < passes; ++p) {
+        uint64_t *dst = (p & 1) ? alt1 : alt0;
+        const int shift = p * kRadixBits;
+        if (kw == 1) {
+            upsweep_kernel<1><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
+            scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
+            downsweep_kernel<1><<<ntiles, kSortThreads, 0, s>>>(src, dst, n, shift, counts, totals,
+                                                                ntiles);
+        } else {
+            upsweep_kernel<2><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
+            scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
+            downsweep_kernel<2><<<ntiles, kSortThreads, 0, s>>>(src, dst, n, shift, counts, totals,
+                                                                ntiles);
+        }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        src = dst;
+    }
+    *result = src;
+    return cudaSuccess;
+}
+
+cudaError_t launch_query(const uint64_t *keys, uint64_t n, int kw, int K, Geometry G,
+                         uint32_t *est, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned g = grid_for(n, 256, 152 * 64);
+    if (kw == 1)
+        query_kernel<1><<<g, 256, 0, s>>>(keys, n, K, G, est);
+    else
+        query_kernel<2><<<g, 256, 0, s>>>(keys, n, K, G, est);
+    return cudaGetLastError();
+}
+
+uint64_t split_scratch_words(uint64_t n) { return (n + kSplitTile - 1) / kSplitTile + 1; }
+
+cudaError_t launch_split(const uint64_t *keys, const uint32_t *est, uint64_t n, int kw,
+                         uint32_t tau, uint64_t *out, uint64_t *scratch, DevCounters *ctr,
+                         cudaStream_t s) {
+    if (n == 0) return cudaMemsetAsync(&ctr->trusted, 0, sizeof(ctr->trusted), s);
+    const uint64_t ntiles = (n + kSplitTile - 1) / kSplitTile;
+    split_count_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(est, n, tau, scratch);
+    split_scan_kernel<<<1, kSortThreads, 0, s>>>(scratch, ntiles, ctr);
+    if (kw == 1)
+        split_scatter_kernel<1><<<(unsigned)ntiles, kSortThreads, 0, s>>>(keys, est, n, tau, scratch,
+                                                                          ctr, out);
+    else
+        split_scatter_kernel<2><<<(unsigned)ntiles, kSortThreads, 0, s>>>(keys, est, n, tau, scratch,
+                                                                          ctr, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge(uint64_t *dst, const uint64_t *src, Geometry G, cudaStream_t s) {
+    merge_kernel<<<grid_for(G.words, 256, 152 * 16), 256, 0, s>>>(dst, src, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_saturated(Geometry G, DevCounters *ctr, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(&ctr->saturated, 0, sizeof(ctr->saturated), s);
+    if (e != cudaSuccess) return e;
+    count_saturated_kernel<<<grid_for(G.words, 256, 152 * 16), 256, 0, s>>>(G, ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace countbf

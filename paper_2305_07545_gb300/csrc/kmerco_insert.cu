@@ -1,0 +1,443 @@
+// Insertion phase of KmerCo (Algorithm 1 with the countBF insert of
+// Algorithm 3) on sm_103a.
+//
+// Work unit: a chunk of kChunk consecutive window starts of the flat bases
+// array, regardless of read boundaries, so long and short reads balance the
+// same way.  Per chunk a block
+//   1. stages the chunk's bases (plus K-1 halo) in shared memory with
+//      16-byte streaming loads,
+//   2. packs them to 2-bit codes (A=0 C=1 G=2 T=3, first base most
+//      significant) with an invalid-base bitmap, and marks read starts in a
+//      break bitmap,
+//   3. keeps the window starts whose K bases are valid and lie in one read,
+//   4. per window: canonical key = min(forward, reverse complement)
+//      (Sections 2.2-2.3), k_h MurmurHash3 hashes, one saturating counter
+//      increment per hash by 64-bit compare-and-swap (Algorithm 3), and an
+//      insert into the distinct-key set (open addressing, linear probing);
+//      keys new to the set are staged in shared memory and appended to the
+//      distinct list with one global atomic per chunk.
+#include "kmerco_internal.cuh"
+
+namespace countbf {
+namespace {
+
+constexpr int kPack32 = kChunk / 16 + 8;   // 16 bases per 32-bit word; chunk + 128 bases
+constexpr int kSpan = kPack32 * 16;        // bases a chunk can stage (>= kChunk + 63)
+constexpr int kRaw = kSpan + 32;
+
+template <int KW>
+struct __align__(16) InsertSmem {
+    uint8_t raw[kRaw];             // raw[head + q] = base q of the chunk
+    uint32_t pk[kPack32];          // codes; word t stored at t ^ 1 so that pairs read as u64
+    uint16_t inv[kPack32];         // bit j of inv[t]: base 16t + j is not ACGTacgt
+    uint32_t brk[kPack32 / 2];     // bit q: a read starts at base q of the chunk
+    uint16_t vpos[kChunk];         // valid window starts
+    uint64_t fresh[kChunk * KW];   // keys new to the distinct set
+    unsigned nvalid;
+    unsigned nfresh;
+    unsigned long long fresh_base;
+};
+
+// 64 bits of a bitmap starting at bit p.
+__device__ __forceinline__ uint64_t bits_at(const uint64_t *bm, unsigned p) {
+    unsigned w = p >> 6, s = p & 63;
+    uint64_t v = bm[w] >> s;
+    if (s) v |= bm[w + 1] << (64 - s);
+    return v;
+}
+
+__device__ __forceinline__ uint64_t load_cg(const uint64_t *p) { return __ldcg(p); }
+
+// 128-bit compare-and-swap (sm_90+), returns the previous slot contents.
+__device__ __forceinline__ void cas128(uint64_t *addr, uint64_t cmp_lo, uint64_t cmp_hi,
+                                       uint64_t new_lo, uint64_t new_hi, uint64_t &old_lo,
+                                       uint64_t &old_hi) {
+    asm volatile(
+        "{\n\t.reg .b128 d, b, c;\n\t"
+        "mov.b128 b, {%3, %4};\n\t"
+        "mov.b128 c, {%5, %6};\n\t"
+        "atom.global.cas.b128 d, [%2], b, c;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t}"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(addr), "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi)
+        : "memory");
+}
+
+// Saturating increment of the counter at `shift` in cell `c`
+// (Algorithm 3: extract, add one unless at 2^alpha - 1, write back).  `old`
+// is a recent read of the cell; a failed CAS refreshes it.
+__device__ __forceinline__ void sat_increment(uint64_t *cells, uint64_t c, unsigned shift,
+                                              uint64_t maxc, uint64_t old, unsigned *err) {
+    const uint64_t inc = 1ull << shift;
+    for (uint32_t it = 0;; ++it) {
+        if (((old >> shift) & maxc) == maxc) return;   // saturated: stays at the maximum
+        uint64_t prev = atomicCAS((unsigned long long *)(cells + c), (unsigned long long)old,
+                                  (unsigned long long)(old + inc));
+        if (prev == old) return;
+        old = prev;
+        if (it >= kCasLimit) {
+            atomicOr(err, kErrCasLimit);
+            return;
+        }
+    }
+}
+
+// Insert a key into the distinct set; true when the key was not there yet.
+template <int KW>
+__device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64_t th,
+                                           uint64_t klo, uint64_t khi, unsigned *err) {
+    uint64_t slot = __umul64hi(th, cap);
+    for (uint32_t it = 0;; ++it) {
+        if (KW == 1) {
+            uint64_t v = load_cg(table + slot);
+            if (v == klo) return false;
+            if (v == kEmptyKey) {
+                uint64_t prev = atomicCAS((unsigned long long *)(table + slot),
+                                          (unsigned long long)kEmptyKey, (unsigned long long)klo);
+                if (prev == kEmptyKey) return true;
+                if (prev == klo) return false;
+            }
+        } else {
+            // 16-byte slots are only ever read through the atomic itself, so
+            // a half-written slot is never mistaken for a key.
+            uint64_t olo, ohi;
+            cas128(table + 2 * slot, kEmptyKey, kEmptyKey, klo, khi, olo, ohi);
+            if (olo == kEmptyKey && ohi == kEmptyKey) return true;
+            if (olo == klo && ohi == khi) return false;
+        }
+        if (++slot == cap) slot = 0;
+        if (it >= kProbeLimit) {
+            atomicOr(err, kErrProbeLimit);
+            return false;
+        }
+    }
+}
+
+template <int KW>
+__global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a) {
+    __shared__ InsertSmem<KW> S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.K;
+    const uint64_t total = a.last - a.first;
+    const Geometry G = a.G;
+    unsigned long long my_windows = 0, my_skipped = 0;
+
+    for (uint64_t chunk = blockIdx.x; chunk < a.nchunks; chunk += gridDim.x) {
+        const uint64_t c0 = chunk * (uint64_t)kChunk;
+        const uint64_t e = min(c0 + (uint64_t)(kChunk + K - 1), total);
+        const unsigned nb = (unsigned)(e - c0);
+        const uintptr_t src = (uintptr_t)(a.bases + c0);
+        const unsigned head = (unsigned)(src & 15);
+        const uintptr_t abase = src - head;
+
+        // 1. stage bytes [c0, e) at raw[head ...]: whole 16-byte vectors
+        //    inside the range with streaming loads, partial ones bytewise.
+        const unsigned nvec = (head + nb + 15) >> 4;
+        for (unsigned v = tid; v < nvec; v += kInsertThreads) {
+            unsigned lo = v << 4, hi = lo + 16;
+            if (lo >= head && hi <= head + nb) {
+                *(uint4 *)(S.raw + lo) = __ldcs((const uint4 *)(abase + lo));
+            } else {
+                for (unsigned b = lo; b < hi; ++b)
+                    if (b >= head && b < head + nb) S.raw[b] = *(const uint8_t *)(abase + b);
+            }
+        }
+        for (int i = tid; i < kPack32 / 2; i += kInsertThreads) S.brk[i] = 0;
+        if (tid == 0) {
+            S.nvalid = 0;
+            S.nfresh = 0;
+        }
+        __syncthreads();
+
+        // 2a. pack: 16 bases per thread -> 2-bit codes + invalid bits
+        for (int t = tid; t < kPack32; t += kInsertThreads) {
+            uint32_t code = 0, bad = 0;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                unsigned q = (unsigned)t * 16 + j;
+                unsigned c = q < nb ? S.raw[head + q] : 'N';
+                unsigned u = c | 0x20u;
+                bool ok = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
+                unsigned cd = ((c >> 1) ^ (c >> 2)) & 3u;   // A,a->0 C,c->1 G,g->2 T,t->3
+                code = (code << 2) | (ok ? cd : 0u);
+                bad |= (ok ? 0u : 1u) << j;
+            }
+            S.pk[t ^ 1] = code;
+            S.inv[t] = (uint16_t)bad;
+        }
+        // 2b. read starts inside the staged span
+        for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; r < a.nreads; r += kInsertThreads) {
+            uint64_t s = a.offsets[r] - a.first;
+            if (s >= c0 + nb) break;
+            if (s < c0) continue;   // only with decreasing offsets, which the host rejects
+            unsigned q = (unsigned)(s - c0);
+            if (q > 0) atomicOr(&S.brk[q >> 5], 1u << (q & 31));
+        }
+        __syncthreads();
+
+        // 3. window starts: inside one read, K valid bases
+        const uint64_t *inv64 = (const uint64_t *)S.inv;
+        const uint64_t *brk64 = (const uint64_t *)S.brk;
+        const uint64_t maskK = K == 64 ? ~0ull : ((1ull << K) - 1);
+        const uint64_t maskK1 = (1ull << (K - 1)) - 1;
+        for (int p0 = 0; p0 < kChunk; p0 += kInsertThreads) {
+            unsigned p = (unsigned)(p0 + tid);
+            bool window = p + (unsigned)K <= nb && (bits_at(brk64, p + 1) & maskK1) == 0;
+            bool valid = window && (bits_at(inv64, p) & maskK) == 0;
+            my_windows += window;
+            my_skipped += window && !valid;
+            unsigned bal = __ballot_sync(0xffffffffu, valid);
+            unsigned base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&S.nvalid, (unsigned)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (valid) S.vpos[base + __popc(bal & ((1u << lane) - 1))] = (uint16_t)p;
+        }
+        __syncthreads();
+
+        // 4. per valid window: canonical key, hashes, counter updates, set insert
+        const unsigned nvalid = S.nvalid;
+        const uint64_t *pk64 = (const uint64_t *)S.pk;
+        for (unsigned i0 = (unsigned)warp * 32; i0 < nvalid; i0 += kInsertThreads) {
+            const unsigned i = i0 + lane;
+            const bool active = i < nvalid;
+            uint64_t klo = 0, khi = 0;
+            if (active) {
+                const unsigned p = S.vpos[i];
+                const unsigned w = p >> 5, s = (p & 31) * 2;
+                const uint64_t x0 = pk64[w], x1 = pk64[w + 1];
+                const uint64_t t0 = s ? (x0 << s) | (x1 >> (64 - s)) : x0;
+                if (KW == 1) {
+                    const uint64_t fwd = t0 >> (64 - 2 * K);
+                    klo = fwd;
+                    if (a.canonical) {
+                        const uint64_t rc = revcomp64(fwd, K);
+                        klo = rc < fwd ? rc : fwd;
+                    }
+                } else {
+                    const uint64_t x2 = pk64[w + 2];
+                    const uint64_t t1 = s ? (x1 << s) | (x2 >> (64 - s)) : x1;
+                    const int r = 128 - 2 * K;   // 0..62
+                    uint64_t fhi, flo;
+                    if (r == 0) {
+                        fhi = t0;
+                        flo = t1;
+                    } else {
+                        flo = (t1 >> r) | (t0 << (64 - r));
+                        fhi = t0 >> r;
+                    }
+                    klo = flo;
+                    khi = fhi;
+                    if (a.canonical) {
+                        uint64_t rhi, rlo;
+                        revcomp128(fhi, flo, K, rhi, rlo);
+                        if (rhi < fhi || (rhi == fhi && rlo < flo)) {
+                            klo = rlo;
+                            khi = rhi;
+                        }
+                    }
+                }
+            }
+
+            uint64_t table_hash = 0;
+            const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
+            for (int a0 = 0; a0 < G.nhash; a0 += 4) {
+                uint64_t cell[4], cur[4];
+                unsigned sh[4];
+                bool use[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    use[j] = active && (a0 + j < G.nhash);
+                    cell[j] = 0;
+                    sh[j] = 0;
+                    if (use[j]) {
+                        uint64_t h1, h2;
+                        if (KW == 1)
+                            murmur8(k1m, (uint32_t)(a0 + j), h1, h2);
+                        else
+                            murmur16(klo, khi, (uint32_t)(a0 + j), h1, h2);
+                        if (a0 + j == 0) table_hash = h2;
+                        locate(G, counter_of(G, h1), cell[j], sh[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (use[j]) cur[j] = load_cg(G.cells + cell[j]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (use[j]) sat_increment(G.cells, cell[j], sh[j], G.maxc, cur[j], &a.ctr->error);
+            }
+
+            bool isnew = false;
+            if (active) isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, &a.ctr->error);
+            const unsigned bal = __ballot_sync(0xffffffffu, isnew);
+            unsigned base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&S.nfresh, (unsigned)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (isnew) {
+                const unsigned slot = base + __popc(bal & ((1u << lane) - 1));
+                S.fresh[slot * KW] = klo;
+                if (KW == 2) S.fresh[slot * KW + 1] = khi;
+            }
+        }
+        __syncthreads();
+
+        // 5. append this chunk's new keys to the distinct list
+        const unsigned nfresh = S.nfresh;
+        if (nfresh) {
+            if (tid == 0) {
+                unsigned long long b = atomicAdd(&a.ctr->distinct, (unsigned long long)nfresh);
+                if (b + nfresh > a.dlist_cap) {
+                    atomicOr(&a.ctr->error, kErrListFull);
+                    b = ~0ull;
+                }
+                S.fresh_base = b;
+            }
+            __syncthreads();
+            const unsigned long long b = S.fresh_base;
+            if (b != ~0ull)
+                for (unsigned i = tid; i < nfresh * KW; i += kInsertThreads)
+                    a.dlist[b * KW + i] = S.fresh[i];
+        }
+        __syncthreads();
+    }
+
+    // totals: one atomic per warp
+    for (int o = 16; o; o >>= 1) {
+        my_windows += __shfl_down_sync(0xffffffffu, my_windows, o);
+        my_skipped += __shfl_down_sync(0xffffffffu, my_skipped, o);
+    }
+    if (lane == 0 && my_windows) {
+        atomicAdd(&a.ctr->windows, my_windows);
+        atomicAdd(&a.ctr->skipped, my_skipped);
+        atomicAdd(&a.ctr->inserted, my_windows - my_skipped);
+    }
+}
+
+// Sum over reads of max(0, len - K + 1); flags decreasing offsets.
+__global__ void window_bound_kernel(const uint64_t *offsets, uint64_t nreads, int K,
+                                    DevCounters *ctr) {
+    unsigned long long sum = 0;
+    bool bad = false;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < nreads;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t s = offsets[r], e = offsets[r + 1];
+        if (e < s) {
+            bad = true;
+            continue;
+        }
+        if (e - s >= (uint64_t)K) sum += e - s - K + 1;
+    }
+    for (int o = 16; o; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&ctr->bound, sum);
+    if (bad) atomicOr(&ctr->bad_offsets, 1u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->first = offsets[0];
+        ctr->last = offsets[nreads];
+    }
+}
+
+// first_read[c] = smallest r in [0, nreads] with offsets[r] - first >= c * kChunk.
+__global__ void first_read_kernel(const uint64_t *offsets, uint64_t nreads, uint64_t first,
+                                  uint64_t nchunks, uint32_t *first_read) {
+    uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (c >= nchunks) return;
+    const uint64_t target = first + c * (uint64_t)kChunk;
+    uint64_t lo = 0, hi = nreads;   // answer in [lo, hi]
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (offsets[mid] >= target)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    first_read[c] = (uint32_t)lo;
+}
+
+// Re-insert keys into a distinct set (growing a set, or merging another
+// handle's keys).  With dlist != nullptr keys new to the set are appended.
+template <int KW>
+__global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *table, uint64_t cap,
+                                uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr) {
+    const int lane = threadIdx.x & 31;
+    for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull; i0 < n;
+         i0 += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = i0 + lane;
+        bool isnew = false;
+        uint64_t klo = 0, khi = 0;
+        if (i < n) {
+            klo = keys[i * KW];
+            khi = KW == 2 ? keys[i * KW + 1] : 0;
+            uint64_t h1, h2;
+            if (KW == 1)
+                murmur8(premix8(klo), 0, h1, h2);
+            else
+                murmur16(klo, khi, 0, h1, h2);
+            isnew = set_insert<KW>(table, cap, h2, klo, khi, &ctr->error);
+        }
+        if (dlist) {
+            const unsigned bal = __ballot_sync(0xffffffffu, isnew);
+            unsigned long long base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&ctr->distinct, (unsigned long long)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (isnew) {
+                const uint64_t slot = base + __popc(bal & ((1u << lane) - 1));
+                if (slot < dlist_cap) {
+                    dlist[slot * KW] = klo;
+                    if (KW == 2) dlist[slot * KW + 1] = khi;
+                } else {
+                    atomicOr(&ctr->error, kErrListFull);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+int insert_blocks_per_sm() {
+    int n1 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, insert_kernel<1>, kInsertThreads, 0);
+    return n1 > 0 ? n1 : 1;
+}
+
+cudaError_t launch_window_bound(const uint64_t *offsets, uint64_t nreads, int K, DevCounters *ctr,
+                                cudaStream_t s) {
+    uint64_t blocks = (nreads + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks == 0) blocks = 1;
+    window_bound_kernel<<<(unsigned)blocks, 256, 0, s>>>(offsets, nreads, K, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t first,
+                              uint64_t nchunks, uint32_t *first_read, cudaStream_t s) {
+    if (nchunks == 0) return cudaSuccess;
+    first_read_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, s>>>(offsets, nreads, first,
+                                                                         nchunks, first_read);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s) {
+    if (a.nchunks == 0) return cudaSuccess;
+    uint64_t g = a.nchunks < (uint64_t)grid ? a.nchunks : (uint64_t)grid;
+    if (a.K <= 32)
+        insert_kernel<1><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
+    else
+        insert_kernel<2><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,
+                            uint64_t cap, uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
+                            cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    uint64_t blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    if (kw == 1)
+        reinsert_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr);
+    else
+        reinsert_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace countbf

@@ -1,0 +1,220 @@
+// Internal declarations of the countBF library: device helpers shared by the
+// kernels and the launchers the host API calls.  Nothing here is part of the
+// public ABI (include/kmerco.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace countbf {
+
+// ---------------------------------------------------------------- constants
+constexpr uint64_t kEmptyKey = ~0ull;      // empty slot of the distinct-key set;
+                                           // no canonical key is all ones
+constexpr int kChunk = 2048;               // window starts per insert work unit
+constexpr int kInsertThreads = 256;
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // keys per radix tile
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSplitTile = 4096;
+constexpr uint32_t kCasLimit = 1u << 22;   // retries of one counter update
+constexpr uint32_t kProbeLimit = 1u << 20; // probes of one distinct-set insert
+
+// Device error bits (DevCounters::error).
+constexpr unsigned kErrCasLimit = 1u;
+constexpr unsigned kErrProbeLimit = 2u;
+constexpr unsigned kErrOffsets = 4u;
+constexpr unsigned kErrListFull = 8u;
+
+// Running totals of a handle, resident on the device.
+struct DevCounters {
+    unsigned long long windows;
+    unsigned long long skipped;
+    unsigned long long inserted;
+    unsigned long long distinct;    // keys appended to the distinct list
+    unsigned long long trusted;     // written by classify
+    unsigned long long bound;       // window upper bound of the last batch
+    unsigned long long first;       // offsets[0] of the last batch
+    unsigned long long last;        // offsets[nreads] of the last batch
+    unsigned long long saturated;   // written by the saturated-counter count
+    unsigned int error;         // sticky kErr* bits
+    unsigned int bad_offsets;   // set by the window-bound kernel
+};
+
+// countBF geometry (Section 2.1): m counters of alpha bits, eta per cell.
+struct Geometry {
+    uint64_t *cells;
+    uint64_t m;          // counters (a multiple of eta)
+    uint64_t words;      // m / eta
+    uint64_t m_mask;     // m - 1 when m is a power of two, else 0
+    uint64_t maxc;       // 2^alpha - 1
+    int alpha;
+    int eta;
+    int eta_log2;        // log2(eta) when eta is a power of two, else -1
+    int nhash;
+};
+
+// ------------------------------------------------------------ hash family
+// H_a(x) = MurmurHash3_x64_128(bytes(x), seed = a).h1 (Appleby's published
+// algorithm).  A K <= 32 key is 8 bytes: no 16-byte block, one tail lane.
+// A 33..64-mer key is 16 bytes: one block, no tail.
+
+__device__ __forceinline__ uint64_t rotl64(uint64_t x, int r) {
+    return (x << r) | (x >> (64 - r));
+}
+
+__device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return k;
+}
+
+constexpr uint64_t kMurC1 = 0x87c37b91114253d5ull;
+constexpr uint64_t kMurC2 = 0x4cf5ad432745937full;
+
+// Lane-1 mix of an 8-byte tail; independent of the seed, so it is computed
+// once per key and reused for all k_h hashes.
+__device__ __forceinline__ uint64_t premix8(uint64_t key) {
+    return rotl64(key * kMurC1, 31) * kMurC2;
+}
+
+// Both output words of MurmurHash3_x64_128 for an 8-byte key whose lane-1
+// mix is k1m.
+__device__ __forceinline__ void murmur8(uint64_t k1m, uint32_t seed, uint64_t &o1,
+                                        uint64_t &o2) {
+    uint64_t h1 = (uint64_t)seed ^ k1m ^ 8ull;
+    uint64_t h2 = (uint64_t)seed ^ 8ull;
+    h1 += h2;
+    h2 += h1;
+    h1 = fmix64(h1);
+    h2 = fmix64(h2);
+    h1 += h2;
+    h2 += h1;
+    o1 = h1;
+    o2 = h2;
+}
+
+// Both output words for a 16-byte key (lo bytes first, then hi).
+__device__ __forceinline__ void murmur16(uint64_t lo, uint64_t hi, uint32_t seed, uint64_t &o1,
+                                         uint64_t &o2) {
+    uint64_t h1 = seed, h2 = seed;
+    uint64_t k1 = rotl64(lo * kMurC1, 31) * kMurC2;
+    h1 ^= k1;
+    h1 = rotl64(h1, 27) + h2;
+    h1 = h1 * 5 + 0x52dce729ull;
+    uint64_t k2 = rotl64(hi * kMurC2, 33) * kMurC1;
+    h2 ^= k2;
+    h2 = rotl64(h2, 31) + h1;
+    h2 = h2 * 5 + 0x38495ab5ull;
+    h1 ^= 16ull;
+    h2 ^= 16ull;
+    h1 += h2;
+    h2 += h1;
+    h1 = fmix64(h1);
+    h2 = fmix64(h2);
+    h1 += h2;
+    h2 += h1;
+    o1 = h1;
+    o2 = h2;
+}
+
+// Counter index g = h mod m (flat form of Algorithm 3's i, j, l addressing).
+__device__ __forceinline__ uint64_t counter_of(const Geometry &G, uint64_t h) {
+    return G.m_mask ? (h & G.m_mask) : (h % G.m);
+}
+
+// Cell and bit shift of counter g: cell g / eta, bits alpha * (g mod eta).
+__device__ __forceinline__ void locate(const Geometry &G, uint64_t g, uint64_t &cell,
+                                       unsigned &shift) {
+    if (G.eta_log2 >= 0) {
+        cell = g >> G.eta_log2;
+        shift = (unsigned)(g & (uint64_t)(G.eta - 1)) * (unsigned)G.alpha;
+    } else {
+        cell = g / (uint64_t)G.eta;
+        shift = (unsigned)(g - cell * (uint64_t)G.eta) * (unsigned)G.alpha;
+    }
+}
+
+// ---------------------------------------------------------------- K-mers
+// Reverse complement of a packed K-mer (K <= 32; the key fills the low 2K
+// bits, first base most significant): complement every 2-bit code (3 - c == ~c), reverse the order of the
+// 2-bit groups, drop the 64 - 2K bits that came from outside the key.
+__device__ __forceinline__ uint64_t revcomp64(uint64_t fwd, int K) {
+    uint64_t r = __brevll(~fwd);   // reverses bits, so each 2-bit group is also flipped
+    r = ((r >> 1) & 0x5555555555555555ull) | ((r & 0x5555555555555555ull) << 1);
+    return r >> (64 - 2 * K);
+}
+
+// Reverse complement of a 33..64-mer held as the 128-bit value hi:lo (low
+// 2K bits used, first base most significant).
+__device__ __forceinline__ void revcomp128(uint64_t hi, uint64_t lo, int K, uint64_t &rhi,
+                                           uint64_t &rlo) {
+    // full 128-bit reverse of ~(hi:lo): new_hi = rev(~lo), new_lo = rev(~hi)
+    uint64_t a = __brevll(~lo), b = __brevll(~hi);
+    a = ((a >> 1) & 0x5555555555555555ull) | ((a & 0x5555555555555555ull) << 1);
+    b = ((b >> 1) & 0x5555555555555555ull) | ((b & 0x5555555555555555ull) << 1);
+    // value occupies the top 2K bits of a:b; shift right by 128 - 2K
+    int s = 128 - 2 * K;           // 0..62 for K in 33..64
+    if (s == 0) {
+        rhi = a;
+        rlo = b;
+    } else {
+        rlo = (b >> s) | (a << (64 - s));
+        rhi = a >> s;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+struct InsertArgs {
+    const uint8_t *bases;        // points at absolute position `first`
+    const uint64_t *offsets;     // nreads + 1 entries
+    uint64_t nreads;
+    uint64_t first, last;        // offsets[0], offsets[nreads]
+    const uint32_t *first_read;  // per chunk: first read starting at or after the chunk
+    uint64_t nchunks;
+    int K;
+    int canonical;
+    Geometry G;
+    uint64_t *table;             // distinct-key set, cap slots of kw words
+    uint64_t cap;
+    uint64_t *dlist;             // distinct keys in arrival order
+    uint64_t dlist_cap;
+    DevCounters *ctr;
+};
+
+cudaError_t launch_window_bound(const uint64_t *offsets, uint64_t nreads, int K,
+                                DevCounters *ctr, cudaStream_t s);
+cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t first,
+                              uint64_t nchunks, uint32_t *first_read, cudaStream_t s);
+cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s);
+int insert_blocks_per_sm();
+// Insert n keys into a distinct set; when dlist is not null, keys new to the
+// set are appended to it (ctr->distinct counts them).
+cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,
+                            uint64_t cap, uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
+                            cudaStream_t s);
+
+// Radix sort of n keys of kw words (1 or 2) on their low `bits` bits.  The
+// sorted keys end in *result, which is one of in, alt0 or alt1; in is left
+// unchanged when passes > 0.  counts needs sort_scratch_words(n, kw) uint32.
+uint64_t sort_scratch_words(uint64_t n, int kw);
+cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint64_t n, int kw,
+                       int bits, uint32_t *counts, const uint64_t **result, cudaStream_t s);
+
+cudaError_t launch_query(const uint64_t *keys, uint64_t n, int kw, int K, Geometry G,
+                         uint32_t *est, cudaStream_t s);
+// est > tau split, stable: trusted keys to out[0, T), erroneous to out[T, n);
+// T written to ctr->trusted.  scratch needs split_scratch_words(n) uint64.
+uint64_t split_scratch_words(uint64_t n);
+cudaError_t launch_split(const uint64_t *keys, const uint32_t *est, uint64_t n, int kw,
+                         uint32_t tau, uint64_t *out, uint64_t *scratch, DevCounters *ctr,
+                         cudaStream_t s);
+cudaError_t launch_merge(uint64_t *dst, const uint64_t *src, Geometry G, cudaStream_t s);
+cudaError_t launch_count_saturated(Geometry G, DevCounters *ctr, cudaStream_t s);
+
+}  // namespace countbf

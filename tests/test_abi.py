@@ -1,0 +1,69 @@
+"""The C-ABI library: it loads, exports every declared entry point, and
+rejects bad arguments on the host before touching the GPU.  CPU only."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2305_07545_gb300 as kc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "kmerco.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kmerco_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return kc.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in kmerco.h but not exported"
+    assert set(names) == set(kc.SIGNATURES)
+
+
+def test_strerror(lib):
+    for code in range(7):
+        assert kc.kmerco_strerror(code)
+    assert kc.kmerco_strerror(99) == "unknown status"
+
+
+@pytest.mark.parametrize("args", [
+    (0, 1 << 10, 4, 3, 2),      # K < 1
+    (65, 1 << 10, 4, 3, 2),     # K > 64
+    (21, 0, 4, 3, 2),           # m < 1
+    (21, 1 << 10, 0, 3, 2),     # alpha < 1
+    (21, 1 << 10, 33, 3, 2),    # alpha > 32
+    (21, 1 << 10, 4, 0, 2),     # k_h < 1
+    (21, 1 << 10, 4, 33, 2),    # k_h > 32
+    (21, 1 << 10, 4, 3, 15),    # tau >= 2^alpha - 1
+    (21, 1 << 10, 1, 3, 1),     # tau >= 2^1 - 1
+])
+def test_create_rejects_bad_parameters(lib, args):
+    h = ctypes.c_void_p(123)
+    assert lib.kmerco_create(*args, ctypes.byref(h)) == kc.EINVAL
+    assert h.value is None
+
+
+def test_null_handle_calls(lib):
+    assert lib.kmerco_insert(None, None, None, 0) == kc.EINVAL
+    assert lib.kmerco_classify(None) == kc.EINVAL
+    assert lib.kmerco_reset(None) == kc.EINVAL
+    assert lib.kmerco_merge(None, None) == kc.EINVAL
+    assert lib.kmerco_stats(None, None) == kc.EINVAL
+    lib.kmerco_destroy(None)
+
+
+def test_python_error_type(lib):
+    with pytest.raises(kc.KmercoError) as e:
+        kc.kmerco_create(21, 1 << 10, 4, 3, 99)
+    assert e.value.status == kc.EINVAL

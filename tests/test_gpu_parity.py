@@ -1,0 +1,280 @@
+"""CUDA path vs the oracle, bit-exact, through the C ABI.
+
+Everything here is integer work, so every comparison is exact: the packed
+countBF cells, the sorted distinct keys, their estimates, the trustworthy
+and erroneous lists and the totals.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import readsim
+
+torch = pytest.importorskip("torch")
+import paper_2305_07545_gb300 as kc  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a: np.ndarray):
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    torch.cuda.synchronize()   # the library runs on its own stream
+    return t
+
+
+def gpu_run(bases, offsets, K, m, alpha, nhash, tau, device_inputs=True, forward_only=False,
+            batches=None):
+    with kc.CountBF(K, m, alpha, nhash, tau, forward_only=forward_only) as bf:
+        parts = batches or [(bases, offsets)]
+        for b, o in parts:
+            if device_inputs:
+                bf.insert(_dev(b), _dev(o))
+            else:
+                bf.insert(b, o)
+        bf.classify()
+        keys, est = bf.distinct()
+        return dict(stats=bf.stats(), counters=bf.counters(), keys=keys, est=est,
+                    trusted=bf.trusted(), erroneous=bf.erroneous())
+
+
+def _split_keys(keys, K):
+    if K <= 32:
+        return np.zeros(len(keys), np.uint64), keys
+    return keys[:, 1].copy(), keys[:, 0].copy()
+
+
+def check(g, bases, offsets, K, alpha, nhash, tau, forward_only=False):
+    st = g["stats"]
+    m = st["m_actual"]
+    ref = oracle.run(bases, offsets, K, m, alpha, nhash, tau, canonical=not forward_only)
+    assert np.array_equal(g["counters"], ref.filter), "countBF cells"
+    hi, lo = _split_keys(g["keys"], K)
+    assert np.array_equal(lo, ref.distinct_lo) and np.array_equal(hi, ref.distinct_hi), "distinct"
+    assert np.array_equal(g["est"].astype(np.uint64), ref.est), "estimates"
+    thi, tlo = _split_keys(g["trusted"], K)
+    ehi, elo = _split_keys(g["erroneous"], K)
+    assert np.array_equal(tlo, ref.distinct_lo[ref.trusted_mask])
+    assert np.array_equal(thi, ref.distinct_hi[ref.trusted_mask])
+    assert np.array_equal(elo, ref.distinct_lo[~ref.trusted_mask])
+    assert np.array_equal(ehi, ref.distinct_hi[~ref.trusted_mask])
+    assert st["windows"] == ref.n_windows
+    assert st["n_skipped"] == ref.n_skipped
+    assert st["inserted"] == ref.n_inserted
+    assert st["distinct"] == len(ref.distinct_lo)
+    assert st["trustworthy"] == int(ref.trusted_mask.sum())
+    assert st["erroneous"] == len(ref.distinct_lo) - int(ref.trusted_mask.sum())
+    maxc = (1 << alpha) - 1
+    eta = 64 // alpha
+    sat = sum(int(((int(w) >> (alpha * l)) & maxc) == maxc) for w in ref.filter for l in range(eta)) \
+        if len(ref.filter) <= 4096 else None
+    if sat is not None:
+        assert st["saturated_counters"] == sat
+    return ref
+
+
+def test_tiny_workload_full_parity():
+    w = readsim.WORKLOADS["tiny"]
+    b, o = w.generate()
+    g = gpu_run(b, o, w.K, w.m, w.alpha, w.nhash, w.tau)
+    ref = check(g, b, o, w.K, w.alpha, w.nhash, w.tau)
+    assert ref.n_skipped > 0 and ref.trusted_mask.any() and (~ref.trusted_mask).any()
+
+
+SWEEP = [
+    # K, m, alpha, nhash, tau
+    (21, 1 << 12, 4, 3, 2),
+    (31, 1000, 4, 4, 3),       # m rounded up to a multiple of eta
+    (17, 999, 5, 2, 1),        # eta = 12, 4 wasted bits, non power-of-two m and eta
+    (11, 4099, 7, 5, 2),
+    (25, 512, 8, 1, 3),
+    (40, 3000, 12, 3, 5),      # two-word keys
+    (55, 1 << 14, 4, 4, 3),    # two-word keys, the long-K workload's K
+    (9, 700, 16, 2, 2),
+    (13, 300, 32, 3, 1),
+    (7, 2048, 1, 3, 0),        # 1-bit counters
+    (5, 64, 2, 6, 1),          # heavy collisions and saturation
+    (1, 16, 4, 2, 1),          # K = 1
+    (32, 1 << 10, 4, 4, 3),    # K = 32, widest one-word key
+    (33, 1 << 10, 4, 4, 3),    # K = 33, narrowest two-word key
+    (64, 1 << 10, 4, 4, 3),    # K = 64
+    (31, 1 << 20, 4, 9, 3),    # k_h not a multiple of 4
+]
+
+
+@pytest.mark.parametrize("K,m,alpha,nhash,tau", SWEEP)
+def test_parameter_sweep(K, m, alpha, nhash, tau):
+    b, o = readsim.random_reads(300, 0, 200, seed=7 * K + m, alphabet=b"ACGTacgtNRY",
+                                weights=[24, 24, 24, 24, 1, 1, 1, 1, 0.3, 0.05, 0.05])
+    g = gpu_run(b, o, K, m, alpha, nhash, tau)
+    check(g, b, o, K, alpha, nhash, tau)
+
+
+@pytest.mark.parametrize("K", [21, 31, 55])
+def test_long_reads_cross_many_chunks(K):
+    b, o = readsim.random_reads(3, 9000, 20000, seed=K, alphabet=b"ACGTN",
+                                weights=[25, 25, 25, 25, 0.02])
+    g = gpu_run(b, o, K, 1 << 16, 4, 4, 3)
+    check(g, b, o, K, 4, 4, 3)
+
+
+def test_many_tiny_and_empty_reads():
+    b, o = readsim.random_reads(20000, 0, 30, seed=3)
+    g = gpu_run(b, o, 21, 1 << 14, 4, 3, 2)
+    ref = check(g, b, o, 21, 4, 3, 2)
+    assert ref.n_inserted > 0
+
+
+def test_repeated_read_contention():
+    # the same read 3000 times: every window hits the same cells and the same
+    # distinct-set slot from many threads at once
+    b, o = readsim.from_strings(["ACGTTGCATTGACCAGTAGGACCATTAGCAGGATTACA"] * 3000)
+    for alpha in (4, 16):
+        g = gpu_run(b, o, 21, 1 << 12, alpha, 4, 3)
+        check(g, b, o, 21, alpha, 4, 3)
+
+
+def test_unaligned_device_slice_and_nonzero_first_offset():
+    b, o = readsim.random_reads(500, 50, 150, seed=11)
+    pad = np.frombuffer(b"NNNNN", np.uint8)
+    b2 = np.concatenate([pad, b])
+    o2 = o + np.uint64(5)
+    tb = _dev(np.concatenate([np.zeros(3, np.uint8), b2]))[3:]   # device pointer not 16-aligned
+    with kc.CountBF(21, 1 << 14, 4, 3, 2) as bf:
+        bf.insert(tb, _dev(o2))
+        bf.classify()
+        keys, est = bf.distinct()
+        g = dict(stats=bf.stats(), counters=bf.counters(), keys=keys, est=est,
+                 trusted=bf.trusted(), erroneous=bf.erroneous())
+    check(g, b2, o2, 21, 4, 3, 2)
+
+
+def test_host_inputs_match_device_inputs():
+    b, o = readsim.scaled("tiny", 800, seed_offset=2).generate()
+    gd = gpu_run(b, o, 21, 1 << 18, 4, 3, 2, device_inputs=True)
+    gh = gpu_run(b, o, 21, 1 << 18, 4, 3, 2, device_inputs=False)
+    for k in ("counters", "keys", "est", "trusted", "erroneous"):
+        assert np.array_equal(gd[k], gh[k]), k
+
+
+def test_batches_accumulate_and_grow_the_distinct_set():
+    b, o = readsim.scaled("tiny", 2000, seed_offset=3).generate()
+    cuts = [0, 10, 300, 2000]   # a small first batch sizes a small set that must grow
+    batches = []
+    for c0, c1 in zip(cuts[:-1], cuts[1:]):
+        ob = o[c0:c1 + 1] - o[c0]
+        batches.append((b[int(o[c0]):int(o[c1])].copy(), ob.copy()))
+    g = gpu_run(b, o, 21, 1 << 20, 4, 3, 2, batches=batches)
+    check(g, b, o, 21, 4, 3, 2)
+    g2 = gpu_run(b, o, 21, 1 << 20, 4, 3, 2, batches=batches, device_inputs=False)
+    assert np.array_equal(g["counters"], g2["counters"])
+
+
+def test_forward_only_strand():
+    b, o = readsim.scaled("tiny", 300).generate()
+    g = gpu_run(b, o, 21, 1 << 16, 4, 3, 2, forward_only=True)
+    check(g, b, o, 21, 4, 3, 2, forward_only=True)
+
+
+def test_query_matches_algorithm_5():
+    b, o = readsim.scaled("tiny", 400).generate()
+    K, m, alpha, nhash = 21, 1 << 14, 4, 3
+    ex = oracle.extract(b, o, K)
+    filt = oracle.insert_sequential(ex.hi, ex.lo, K, m, alpha, nhash)
+    probe = np.concatenate([ex.lo[:500], readsim.Stream(5).integers(500, 1 << 42).astype(np.uint64)])
+    with kc.CountBF(K, m, alpha, nhash, 2) as bf:
+        bf.insert(b, o)
+        est = bf.query(probe)
+        est_dev = torch.zeros(len(probe), dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        kc.kmerco_query(bf.h, _dev(probe), len(probe), est_dev)
+    want = [oracle.query(filt, K, 0, int(x), m, alpha, nhash) for x in probe]
+    assert est.tolist() == want
+    assert est_dev.cpu().numpy().view(np.uint32).tolist() == want
+    assert any(v == 0 for v in want[500:])
+
+
+def test_merge_equals_single_handle():
+    b, o = readsim.scaled("tiny", 1200, seed_offset=4).generate()
+    half = 500
+    b1, o1 = b[:int(o[half])].copy(), o[:half + 1].copy()
+    b2, o2 = b[int(o[half]):].copy(), (o[half:] - o[half]).copy()
+    with kc.CountBF(21, 1 << 16, 4, 3, 2) as x, kc.CountBF(21, 1 << 16, 4, 3, 2) as y:
+        x.insert(_dev(b1), _dev(o1))
+        y.insert(_dev(b2), _dev(o2))
+        x.merge(y)
+        x.classify()
+        keys, est = x.distinct()
+        g = dict(stats=x.stats(), counters=x.counters(), keys=keys, est=est,
+                 trusted=x.trusted(), erroneous=x.erroneous())
+    check(g, b, o, 21, 4, 3, 2)
+    with kc.CountBF(21, 1 << 16, 4, 3, 2) as x, kc.CountBF(31, 1 << 16, 4, 3, 2) as y:
+        with pytest.raises(kc.KmercoError):
+            x.merge(y)
+
+
+def test_reset_reuse_and_states():
+    b, o = readsim.scaled("tiny", 300).generate()
+    with kc.CountBF(21, 1 << 16, 4, 3, 2) as bf:
+        with pytest.raises(kc.KmercoError) as e:
+            bf.distinct()
+        assert e.value.status == kc.ESTATE
+        bf.insert(_dev(b), _dev(o))
+        bf.classify()
+        first = bf.counters(), bf.distinct()[0]
+        n = kc.kmerco_get_distinct(bf.h)
+        small = np.zeros(max(n - 1, 1), np.uint64)
+        with pytest.raises(kc.KmercoError) as e:
+            kc.kmerco_get_distinct(bf.h, small, None, n - 1)
+        assert e.value.status == kc.ESIZE
+        bf.reset()
+        assert not bf.counters().any()
+        bf.insert(_dev(b), _dev(o))
+        bf.classify()
+        assert np.array_equal(bf.counters(), first[0])
+        assert np.array_equal(bf.distinct()[0], first[1])
+
+
+def test_empty_and_too_short_inputs():
+    for reads in ([], [""], ["ACGT", "AC", ""], ["N" * 50]):
+        b, o = readsim.from_strings(reads)
+        g = gpu_run(b, o, 21, 1 << 10, 4, 3, 2, device_inputs=False)
+        ref = check(g, b, o, 21, 4, 3, 2)
+        assert ref.n_inserted == 0
+
+
+def test_decreasing_offsets_rejected():
+    b, o = readsim.from_strings(["ACGTACGTACGTACGTACGTACGT"] * 3)
+    bad = o.copy()
+    bad[1], bad[2] = bad[2], bad[1]
+    with kc.CountBF(5, 1 << 10, 4, 3, 2) as bf:
+        for dev in (False, True):
+            with pytest.raises(kc.KmercoError) as e:
+                if dev:
+                    bf.insert(_dev(b), _dev(bad))
+                else:
+                    bf.insert(b, bad)
+            assert e.value.status == kc.EINVAL
+        bf.insert(_dev(b), _dev(o))   # the handle stays usable
+        bf.classify()
+        assert bf.stats()["inserted"] == 3 * 20
+
+
+@pytest.mark.slow
+def test_single_sample_workload_full_size():
+    """The 1M-read, 2^28-counter workload the benchmark times, bit-exact."""
+    w = readsim.WORKLOADS["single"]
+    b, o = w.generate()
+    g = gpu_run(b, o, w.K, w.m, w.alpha, w.nhash, w.tau)
+    st = g["stats"]
+    ex = oracle.extract(b, o, w.K)
+    assert st["windows"] == ex.n_windows and st["inserted"] == ex.n
+    filt = oracle.counters_closed_form(ex.hi, ex.lo, w.K, w.m, w.alpha, w.nhash)
+    assert np.array_equal(g["counters"], filt)
+    dhi, dlo, _ = oracle.distinct(ex.hi, ex.lo)
+    assert np.array_equal(g["keys"], dlo)
+    est, tr = oracle.classify(filt, dhi, dlo, w.K, w.m, w.alpha, w.nhash, w.tau)
+    assert np.array_equal(g["est"].astype(np.uint64), est)
+    assert np.array_equal(g["trusted"], dlo[tr])
+    assert np.array_equal(g["erroneous"], dlo[~tr])
