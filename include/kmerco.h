@@ -186,6 +186,45 @@ int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est);
  */
 int kmerco_merge(kmerco_t *dst, kmerco_t *src);
 
+/*
+ * Allocation-free classification.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory themselves
+ * -- a process whose GPU memory is all reserved up front by its own pool
+ * allocator (a serving stack, a framework that owns the device), a plug-in
+ * running inside such a host, or a latency-bound path that cannot afford
+ * cudaMalloc/cudaFree, which may synchronise the whole device.
+ *
+ * It computes over caller-owned device buffers what kmerco_classify()
+ * computes for a handle:
+ *   est[i] = QcountBF-II of keys[i] against the countBF `cells` (m counters
+ *            of counter_bits bits, laid out as kmerco_get_counters() returns
+ *            them), k_h = nhash hash functions, K = k;
+ *   out    = the keys with est > threshold, in input order, followed by the
+ *            keys with est <= threshold, in input order (sorted input gives
+ *            two sorted lists);
+ *   *n_trusted (host memory) = the number of keys with est > threshold.
+ * cells, keys (n keys of 1 word for k <= 32, 2 words low-first otherwise),
+ * est (n uint32) and out (n keys) are device memory on the current device.
+ * m must be a multiple of floor(64 / counter_bits), e.g. stats.m_actual.
+ *
+ * Nothing is allocated.  The only scratch is one fixed device array of
+ * KMERCO_NOALLOC_MAX_KEYS / 4096 + 1 uint64 (512 KiB + 8 bytes) that every
+ * GPU loading this library holds until the process exits.  Hence:
+ *  - n above KMERCO_NOALLOC_MAX_KEYS returns KMERCO_EINVAL before any GPU
+ *    work;
+ *  - every call shares that array, so calls that overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller;
+ *  - the first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress; make that first call before any stream capture.
+ * Runs on `stream` (a cudaStream_t; NULL is the legacy default stream) and
+ * synchronises it before returning.  Errors: EINVAL (argument out of range,
+ * NULL pointer, n too large), ECUDA.
+ */
+#define KMERCO_NOALLOC_MAX_KEYS 268435456ull
+int kmerco_classify_noalloc(const uint64_t *cells, uint64_t m, int k, int counter_bits,
+                            int nhash, uint32_t threshold, const uint64_t *keys, uint64_t n,
+                            uint32_t *est, uint64_t *out, uint64_t *n_trusted, void *stream);
+
 /* Zero the countBF, empty the distinct set and all totals; keeps memory. */
 int kmerco_reset(kmerco_t *h);
 

@@ -68,7 +68,11 @@ SIGNATURES = {
     "kmerco_merge": (c_int, [c_void_p, c_void_p]),
     "kmerco_reset": (c_int, [c_void_p]),
     "kmerco_strerror": (c_char_p, [c_int]),
+    "kmerco_classify_noalloc": (c_int, [c_void_p, c_uint64, c_int, c_int, c_int, c_uint32,
+                                        c_void_p, c_uint64, c_void_p, c_void_p, _u64p, c_void_p]),
 }
+
+NOALLOC_MAX_KEYS = 1 << 28
 
 
 def load(build: bool = True) -> ctypes.CDLL:
@@ -189,6 +193,18 @@ def kmerco_merge(dst: int, src: int) -> None:
 
 def kmerco_reset(h: int) -> None:
     _check(load().kmerco_reset(h), "kmerco_reset")
+
+
+def kmerco_classify_noalloc(cells, m: int, k: int, counter_bits: int, nhash: int,
+                            threshold: int, keys, n: int, est, out, stream: int | None = None) -> int:
+    """Classification over caller-owned device buffers without any allocation
+    (for callers that cannot allocate device memory); returns the number of
+    trustworthy keys.  See kmerco.h for the contract and its limits."""
+    nt = c_uint64(0)
+    _check(load().kmerco_classify_noalloc(_ptr(cells), m, k, counter_bits, nhash, threshold,
+                                          _ptr(keys), n, _ptr(est), _ptr(out), byref(nt),
+                                          stream or None), "kmerco_classify_noalloc")
+    return nt.value
 
 
 # ------------------------------------------------------------------ wrapper
