@@ -170,6 +170,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Largest value of x over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, steps: int, world: int, slowest_s: float) -> float:
+    """Units all ranks processed divided by the slowest rank's time (weak scaling:
+    every rank processes its own sample of the same size)."""
+    return units_per_rank_step * steps * world / slowest_s
+
+
 def run_reference(args) -> None:
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -214,7 +231,7 @@ def run_ours(args) -> None:
         torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
     w = readsim.WORKLOADS[args.workload]
-    wl = readsim.scaled(args.workload, w.reads.n_reads, seed_offset=rank)
+    wl = readsim.scaled(args.workload, args.reads or w.reads.n_reads, seed_offset=rank)
     bases, offsets = wl.generate()
     nreads = len(offsets) - 1
     lens = np.diff(offsets.astype(np.int64))
@@ -259,13 +276,10 @@ def run_ours(args) -> None:
             assert (s["inserted"], s["distinct"], s["trustworthy"]) == (inserted, distinct, trusted)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dev)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        total_ms = float(t.item())
-    value = inserted * args.steps * world / (total_ms / 1000.0)
+    value = whole_job_rate(inserted, args.steps, world, total_ms / 1000.0)
 
     # end to end through the public API with host (pinned) buffers
     e2e = None
@@ -293,13 +307,9 @@ def run_ours(args) -> None:
         for _ in range(args.steps):
             nt, ne = e2e_step()
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         assert nt == trusted and nt + ne == distinct
-        e2e = {"value": inserted * args.steps * world / e2e_s, "unit": UNIT,
+        e2e = {"value": whole_job_rate(inserted, args.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(bases.nbytes + offsets.nbytes),
                "d2h_bytes_per_step": int(8 * distinct),
                "note": "reset + insert from pinned host reads + classify + copy of the "
@@ -332,7 +342,7 @@ def run_ours(args) -> None:
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": describe(w), "K": w.K, "m": w.m, "counter_bits": w.alpha,
+            "config": {"workload": describe(wl), "K": w.K, "m": w.m, "counter_bits": w.alpha,
                        "nhash": w.nhash, "tau": w.tau, "reads_per_gpu": nreads,
                        "kmers_per_step_per_gpu": inserted, "distinct_per_gpu": distinct,
                        "trustworthy_per_gpu": trusted,
@@ -357,6 +367,8 @@ def main(argv=None) -> None:
                     help="reads in the bounded CPU-oracle sample")
     ap.add_argument("--ref-reads", type=int, default=25_000,
                     help="reads per step of the reference (oracle) arm")
+    ap.add_argument("--reads", type=int, default=0,
+                    help="reads per GPU (default: the workload's own count; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
