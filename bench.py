@@ -35,7 +35,7 @@ METRIC = "K-mer insertions/sec on 1 GB300 (bit-exact vs oracle); % of L2-atomic/
 UNIT = "K-mer insertions/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "insert_kernel_single.json")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "insert_kernel_single.md")
 INSERT_SOURCES = [os.path.join(ROOT, "paper_2305_07545_gb300", "csrc", f)
                   for f in ("kmerco_insert.cu", "kmerco_internal.cuh")]
 
@@ -77,9 +77,11 @@ def recorded_traffic() -> float | None:
     taken on the current insert-kernel source."""
     try:
         with open(PROFILE_SUMMARY) as f:
-            s = json.load(f)
-        if s.get("source_sha") == source_sha():
-            return float(s["dram_bytes_per_launch"])
+            for line in f:
+                if line.startswith("traffic_record"):
+                    kv = dict(p.split("=", 1) for p in line.split()[1:])
+                    if kv.get("source_sha") == source_sha():
+                        return float(kv["dram_bytes_per_launch"])
     except Exception:
         pass
     return None

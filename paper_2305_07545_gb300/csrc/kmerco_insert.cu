@@ -48,6 +48,27 @@ __device__ __forceinline__ uint64_t bits_at(const uint64_t *bm, unsigned p) {
 
 __device__ __forceinline__ uint64_t load_cg(const uint64_t *p) { return __ldcg(p); }
 
+// L2 eviction-priority policies.  The countBF is kept (evict_last) while
+// the distinct set, touched once per window at random over a region much
+// larger than L2, is let go first.
+__device__ __forceinline__ uint64_t policy_keep() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_stream() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// 64-bit load that bypasses L1 (the value may be changed by other SMs'
+// atomics) with an L2 eviction policy.
+__device__ __forceinline__ uint64_t load_hint(const uint64_t *a, uint64_t pol) {
+    uint64_t v;
+    asm volatile("ld.global.cg.L2::cache_hint.b64 %0, [%1], %2;" : "=l"(v) : "l"(a), "l"(pol) : "memory");
+    return v;
+}
+
 // 128-bit compare-and-swap (sm_90+), returns the previous slot contents.
 __device__ __forceinline__ void cas128(uint64_t *addr, uint64_t cmp_lo, uint64_t cmp_hi,
                                        uint64_t new_lo, uint64_t new_hi, uint64_t &old_lo,
@@ -83,13 +104,16 @@ __device__ __forceinline__ void sat_increment(uint64_t *cells, uint64_t c, unsig
 }
 
 // Insert a key into the distinct set; true when the key was not there yet.
+// For one-word keys `first` is an already loaded value of the home slot
+// (kEmptyKey - 1 when none was loaded, a value no key or empty slot has).
 template <int KW>
 __device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64_t th,
-                                           uint64_t klo, uint64_t khi, unsigned *err) {
+                                           uint64_t klo, uint64_t khi, unsigned *err,
+                                           uint64_t pol, uint64_t first = kEmptyKey - 1) {
     uint64_t slot = __umul64hi(th, cap);
     for (uint32_t it = 0;; ++it) {
         if (KW == 1) {
-            uint64_t v = load_cg(table + slot);
+            uint64_t v = (it == 0 && first != kEmptyKey - 1) ? first : load_hint(table + slot, pol);
             if (v == klo) return false;
             if (v == kEmptyKey) {
                 uint64_t prev = atomicCAS((unsigned long long *)(table + slot),
@@ -120,6 +144,7 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
     const int K = a.K;
     const uint64_t total = a.last - a.first;
     const Geometry G = a.G;
+    const uint64_t pol_keep = policy_keep(), pol_stream = policy_stream();
     unsigned long long my_windows = 0, my_skipped = 0;
 
     for (uint64_t chunk = blockIdx.x; chunk < a.nchunks; chunk += gridDim.x) {
@@ -238,12 +263,15 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
                 }
             }
 
-            uint64_t table_hash = 0;
+            // All loads of a group of four hashes (and, in the first group,
+            // the distinct-set home slot) are issued together, then all
+            // first compare-and-swap attempts; only failed attempts retry.
+            uint64_t table_hash = 0, table_first = kEmptyKey - 1;
             const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
             for (int a0 = 0; a0 < G.nhash; a0 += 4) {
-                uint64_t cell[4], cur[4];
+                uint64_t cell[4], cur[4], prev[4];
                 unsigned sh[4];
-                bool use[4];
+                bool use[4], need[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     use[j] = active && (a0 + j < G.nhash);
@@ -259,16 +287,30 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
                         locate(G, counter_of(G, h1), cell[j], sh[j]);
                     }
                 }
+                if (KW == 1 && a0 == 0 && active)
+                    table_first = load_hint(a.table + __umul64hi(table_hash, a.cap), pol_stream);
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (use[j]) cur[j] = load_cg(G.cells + cell[j]);
+                    if (use[j]) cur[j] = load_hint(G.cells + cell[j], pol_keep);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    need[j] = use[j] && ((cur[j] >> sh[j]) & G.maxc) != G.maxc;
+                    prev[j] = cur[j];
+                    if (need[j])
+                        prev[j] = atomicCAS((unsigned long long *)(G.cells + cell[j]),
+                                            (unsigned long long)cur[j],
+                                            (unsigned long long)(cur[j] + (1ull << sh[j])));
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (use[j]) sat_increment(G.cells, cell[j], sh[j], G.maxc, cur[j], &a.ctr->error);
+                    if (need[j] && prev[j] != cur[j])
+                        sat_increment(G.cells, cell[j], sh[j], G.maxc, prev[j], &a.ctr->error);
             }
 
             bool isnew = false;
-            if (active) isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, &a.ctr->error);
+            if (active)
+                isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, &a.ctr->error,
+                                       pol_stream, table_first);
             const unsigned bal = __ballot_sync(0xffffffffu, isnew);
             unsigned base = 0;
             if (lane == 0 && bal) base = atomicAdd(&S.nfresh, (unsigned)__popc(bal));
@@ -372,7 +414,7 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
                 murmur8(premix8(klo), 0, h1, h2);
             else
                 murmur16(klo, khi, 0, h1, h2);
-            isnew = set_insert<KW>(table, cap, h2, klo, khi, &ctr->error);
+            isnew = set_insert<KW>(table, cap, h2, klo, khi, &ctr->error, policy_stream());
         }
         if (dlist) {
             const unsigned bal = __ballot_sync(0xffffffffu, isnew);
