@@ -70,6 +70,11 @@ typedef struct {
     void *stream;          /* cudaStream_t to run on; NULL: the library creates its own */
     uint64_t hbm_budget;   /* bytes of device memory the handle may hold; 0: no limit */
     int device;            /* CUDA device ordinal; -1: the current device */
+    int update_mode;       /* how counter increments reach the countBF (same result either way):
+                              0 automatic; 1 atomic compare-and-swap on each 64-bit cell;
+                              2 partitioned: increments grouped by countBF slice and applied in
+                              shared memory (needs k <= 32, nhash <= 4, at most 2^26 cells;
+                              otherwise create returns EINVAL) */
 } kmerco_config_t;
 
 /* Running totals and results of one handle (kmerco_stats). */

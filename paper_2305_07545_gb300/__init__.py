@@ -27,7 +27,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ESIZE = range(7)
 class kmerco_config_t(ctypes.Structure):
     _fields_ = [("k", c_int), ("m", c_uint64), ("counter_bits", c_int), ("nhash", c_int),
                 ("threshold", c_uint32), ("forward_only", c_int), ("stream", c_void_p),
-                ("hbm_budget", c_uint64), ("device", c_int)]
+                ("hbm_budget", c_uint64), ("device", c_int), ("update_mode", c_int)]
 
 
 class kmerco_stats_t(ctypes.Structure):
@@ -130,11 +130,14 @@ def kmerco_create(k: int, m: int, counter_bits: int, nhash: int, threshold: int)
     return h.value
 
 
+UPDATE_AUTO, UPDATE_ATOMIC, UPDATE_PARTITIONED = 0, 1, 2
+
+
 def kmerco_create_ex(k: int, m: int, counter_bits: int, nhash: int, threshold: int,
                      forward_only: bool = False, stream: int | None = None,
-                     hbm_budget: int = 0, device: int = -1) -> int:
+                     hbm_budget: int = 0, device: int = -1, update_mode: int = 0) -> int:
     cfg = kmerco_config_t(k, m, counter_bits, nhash, threshold, int(forward_only),
-                          stream or None, hbm_budget, device)
+                          stream or None, hbm_budget, device, update_mode)
     h = c_void_p()
     _check(load().kmerco_create_ex(byref(cfg), byref(h)), "kmerco_create_ex")
     return h.value
@@ -217,11 +220,11 @@ class CountBF:
 
     def __init__(self, k: int, m: int, counter_bits: int = 4, nhash: int = 4,
                  threshold: int = 3, forward_only: bool = False, stream: int | None = None,
-                 hbm_budget: int = 0, device: int = -1):
+                 hbm_budget: int = 0, device: int = -1, update_mode: int = UPDATE_AUTO):
         self.k = k
         self.kw = 1 if k <= 32 else 2
         self.h = kmerco_create_ex(k, m, counter_bits, nhash, threshold, forward_only, stream,
-                                  hbm_budget, device)
+                                  hbm_budget, device, update_mode)
 
     def close(self) -> None:
         if self.h:

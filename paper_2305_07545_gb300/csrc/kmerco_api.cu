@@ -19,7 +19,8 @@ struct kmerco {
     int device;
     cudaStream_t stream;
     bool own_stream;
-    int insert_grid;
+    int update_mode;         // 0 automatic, 1 atomic, 2 partitioned
+    int grid_atomic, grid_part;
     uint64_t budget, used;
     Geometry G;
     DevCounters *ctr;        // device
@@ -54,6 +55,12 @@ struct kmerco {
     cudaEvent_t ev[4];
     bool insert_timed, classify_timed;
     uint64_t launches;       // kernels launched by this handle
+    uint32_t *coarse;        // partitioned design: increment codes per coarse region
+    uint64_t coarse_alloc;
+    uint32_t *fine;          // ... and per slice
+    uint64_t fine_alloc;
+    unsigned long long *part_ctr;   // region cursors and written counts
+    uint64_t part_ctr_alloc;
 };
 
 namespace {
@@ -190,7 +197,29 @@ int validate(const kmerco_config_t *c) {
     const uint64_t maxc = (1ull << c->counter_bits) - 1;
     if ((uint64_t)c->threshold >= maxc) return KMERCO_EINVAL;
     if (c->forward_only != 0 && c->forward_only != 1) return KMERCO_EINVAL;
+    if (c->update_mode < 0 || c->update_mode > 2) return KMERCO_EINVAL;
+    if (c->update_mode == 2) {
+        const uint64_t eta = 64 / (uint64_t)c->counter_bits;
+        const uint64_t words = (c->m + eta - 1) / eta;
+        if (c->k > 32 || c->nhash > kPartMaxHash || words > (1ull << (kMaxCoarseShift + 6)))
+            return KMERCO_EINVAL;
+    }
     return KMERCO_OK;
+}
+
+// Whether this handle applies counter increments with the partitioned design.
+bool use_partitioned(const kmerco_t *h) {
+    if (h->update_mode == 1) return false;
+    const bool able = h->kw == 1 && h->nhash <= kPartMaxHash &&
+                      h->G.words <= (1ull << (kMaxCoarseShift + 6));
+    if (h->update_mode == 2) return able;
+    return able && h->G.words >= (1ull << 17);   // smaller countBFs stay L2-resident
+}
+
+int ceil_log2(uint64_t x) {
+    int l = 0;
+    while ((1ull << l) < x) ++l;
+    return l;
 }
 
 }  // namespace
@@ -262,7 +291,10 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
         if (status) break;
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-        h->insert_grid = (sms > 0 ? sms : 1) * insert_blocks_per_sm();
+        if (sms <= 0) sms = 1;
+        h->update_mode = cfg->update_mode;
+        h->grid_atomic = sms * insert_blocks_per_sm(h->kw, false);
+        h->grid_part = sms * insert_blocks_per_sm(1, true);
 
         const uint64_t eta = (uint64_t)h->eta;
         Geometry &G = h->G;
@@ -322,6 +354,9 @@ void kmerco_destroy(kmerco_t *h) {
         dev_free(h, h->split_scratch, h->split_scratch_cap * 8);
         dev_free(h, h->q_keys, h->q_cap * 16);
         dev_free(h, h->q_est, h->q_cap * 4);
+        dev_free(h, h->coarse, h->coarse_alloc * 4);
+        dev_free(h, h->fine, h->fine_alloc * 4);
+        dev_free(h, h->part_ctr, h->part_ctr_alloc * 8);
         if (h->ctr_host) cudaFreeHost(h->ctr_host);
         for (int i = 0; i < 4; ++i)
             if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -391,9 +426,37 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     }
     if (bound == 0) return KMERCO_OK;   // no window fits in any read
     KM_TRY(ensure_set_capacity(h, bound));
-    const uint64_t nchunks = (nbytes + kChunk - 1) / kChunk;
+
+    // Partitioned design: size the increment-code buffers for this batch (the
+    // atomic design takes over when they cannot be had).
+    bool part = use_partitioned(h);
+    int coarse_shift = 0, slice_shift = 0;
+    uint64_t coarse_cap = 0, fine_cap = 0, nslices = 0;
+    bool repart = false;
+    if (part) {
+        const uint64_t W = h->G.words, U = bound * (uint64_t)h->nhash;
+        coarse_shift = ceil_log2(W) - 6;
+        if (coarse_shift < 0) coarse_shift = 0;
+        repart = coarse_shift > kSliceShift;
+        slice_shift = repart ? kSliceShift : coarse_shift;
+        nslices = (W + (1ull << slice_shift) - 1) >> slice_shift;
+        coarse_cap = U / kCoarseBins;
+        coarse_cap += coarse_cap / 6 + 4096;
+        fine_cap = repart ? U / nslices : 0;
+        fine_cap += fine_cap / 5 + 1024;
+        if (U > (1ull << 31) ||
+            ensure(h, &h->coarse, &h->coarse_alloc, kCoarseBins * coarse_cap) != KMERCO_OK ||
+            (repart && ensure(h, &h->fine, &h->fine_alloc, nslices * fine_cap) != KMERCO_OK) ||
+            ensure(h, &h->part_ctr, &h->part_ctr_alloc, 2 * kCoarseBins + 2 * nslices) != KMERCO_OK)
+            part = false;
+        else
+            KM_CUDA(cudaMemsetAsync(h->part_ctr, 0, (2 * kCoarseBins + 2 * nslices) * 8, h->stream));
+    }
+
+    const uint64_t chunk = part ? kPartChunk : kChunk;
+    const uint64_t nchunks = (nbytes + chunk - 1) / chunk;
     KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, nchunks));
-    KM_CUDA(launch_first_read(d_off, nreads, first, nchunks, h->first_read, h->stream));
+    KM_CUDA(launch_first_read(d_off, nreads, first, nchunks, chunk, h->first_read, h->stream));
     h->launches += nchunks ? 1 : 0;
 
     InsertArgs a;
@@ -412,9 +475,43 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     a.dlist = h->dlist;
     a.dlist_cap = h->dlist_cap;
     a.ctr = h->ctr;
+    a.part = part ? 1 : 0;
+    a.coarse_shift = coarse_shift;
+    a.coarse = h->coarse;
+    a.coarse_cap = coarse_cap;
+    a.coarse_cursor = h->part_ctr;
+    a.coarse_written = h->part_ctr ? h->part_ctr + kCoarseBins : nullptr;
     KM_CUDA(cudaEventRecord(h->ev[0], h->stream));
-    KM_CUDA(launch_insert(a, h->insert_grid, h->stream));
+    KM_CUDA(launch_insert(a, part ? h->grid_part : h->grid_atomic, h->stream));
     h->launches += nchunks ? 1 : 0;
+    if (part) {
+        unsigned long long *fine_cursor = h->part_ctr + 2 * kCoarseBins;
+        unsigned long long *fine_written = fine_cursor + nslices;
+        if (repart) {
+            PartArgs p;
+            p.G = h->G;
+            p.coarse_shift = coarse_shift;
+            p.coarse = h->coarse;
+            p.coarse_cap = coarse_cap;
+            p.coarse_written = a.coarse_written;
+            p.fine = h->fine;
+            p.fine_cap = fine_cap;
+            p.fine_cursor = fine_cursor;
+            p.fine_written = fine_written;
+            p.ctr = h->ctr;
+            KM_CUDA(launch_repartition(p, h->stream));
+            h->launches += 1;
+        }
+        ApplyArgs ap;
+        ap.G = h->G;
+        ap.slice_shift = slice_shift;
+        ap.codes = repart ? h->fine : h->coarse;
+        ap.cap = repart ? fine_cap : coarse_cap;
+        ap.written = repart ? fine_written : a.coarse_written;
+        ap.ctr = h->ctr;
+        KM_CUDA(launch_apply(ap, nslices, h->stream));
+        h->launches += 1;
+    }
     KM_CUDA(cudaEventRecord(h->ev[1], h->stream));
     h->insert_timed = true;
     h->classified = false;

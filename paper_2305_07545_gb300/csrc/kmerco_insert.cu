@@ -16,25 +16,50 @@
 //      insert into the distinct-key set (open addressing, linear probing);
 //      keys new to the set are staged in shared memory and appended to the
 //      distinct list with one global atomic per chunk.
+//
+// Two designs apply the counter increments of step 4:
+//  - atomic: each increment is a compare-and-swap on its 64-bit cell in
+//    global memory (any geometry);
+//  - partitioned (one-word keys, k_h <= 4, at most 2^26 cells): each
+//    increment is emitted as a 32-bit code; the chunk's codes are
+//    counting-sorted in shared memory into 64 coarse countBF regions and
+//    appended to per-region buffers with one cursor atomic per region and
+//    chunk.  repartition_kernel splits every coarse region into slices of
+//    2^14 cells (128 KiB), and apply_kernel loads one slice per block into
+//    shared memory, applies its increments there with shared-memory
+//    compare-and-swap and writes the slice back once.  Increments that do
+//    not fit a buffer fall back to the global compare-and-swap.
+// Saturating increments commute, so both designs give the same countBF.
 #include "kmerco_internal.cuh"
 
 namespace countbf {
 namespace {
 
-constexpr int kPack32 = kChunk / 16 + 8;   // 16 bases per 32-bit word; chunk + 128 bases
-constexpr int kSpan = kPack32 * 16;        // bases a chunk can stage (>= kChunk + 63)
-constexpr int kRaw = kSpan + 32;
+// Staging sizes for a chunk of CHUNK window starts.
+template <int CHUNK>
+struct ChunkDims {
+    static constexpr int kPack32 = CHUNK / 16 + 8;   // 16 bases per 32-bit word; chunk + 128 bases
+    static constexpr int kRaw = kPack32 * 16 + 32;   // >= CHUNK + 63 bases + alignment slack
+};
 
-template <int KW>
+template <int KW, int CHUNK, bool PART>
 struct __align__(16) InsertSmem {
-    uint8_t raw[kRaw];             // raw[head + q] = base q of the chunk
-    uint32_t pk[kPack32];          // codes; word t stored at t ^ 1 so that pairs read as u64
-    uint16_t inv[kPack32];         // bit j of inv[t]: base 16t + j is not ACGTacgt
-    uint32_t brk[kPack32 / 2];     // bit q: a read starts at base q of the chunk
-    uint16_t vpos[kChunk];         // valid window starts
-    uint64_t fresh[kChunk * KW];   // keys new to the distinct set
+    uint8_t raw[ChunkDims<CHUNK>::kRaw];        // raw[head + q] = base q of the chunk
+    uint32_t pk[ChunkDims<CHUNK>::kPack32];     // codes; word t at t ^ 1 so pairs read as u64
+    uint16_t inv[ChunkDims<CHUNK>::kPack32];    // bit j of inv[t]: base 16t + j is not ACGTacgt
+    uint32_t brk[ChunkDims<CHUNK>::kPack32 / 2];  // bit q: a read starts at base q of the chunk
+    uint16_t vpos[CHUNK];                       // valid window starts
+    uint64_t fresh[CHUNK * KW];                 // keys new to the distinct set
+    // partitioned design: the chunk's counter-increment codes
+    uint32_t staged[PART ? CHUNK * kPartMaxHash : 1];
+    uint32_t sorted[PART ? CHUNK * kPartMaxHash : 1];
+    unsigned hist[PART ? kCoarseBins : 1];
+    unsigned start[PART ? kCoarseBins : 1];
+    unsigned fill[PART ? kCoarseBins : 1];
+    unsigned long long base[PART ? kCoarseBins : 1];
     unsigned nvalid;
     unsigned nfresh;
+    unsigned nupd;
     unsigned long long fresh_base;
 };
 
@@ -137,9 +162,22 @@ __device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64
     }
 }
 
-template <int KW>
+// Cell and counter index of counter g (cell g / eta, counter g mod eta).
+__device__ __forceinline__ void locate_slot(const Geometry &G, uint64_t g, uint64_t &cell,
+                                            unsigned &slot) {
+    if (G.eta_log2 >= 0) {
+        cell = g >> G.eta_log2;
+        slot = (unsigned)(g & (uint64_t)(G.eta - 1));
+    } else {
+        cell = g / (uint64_t)G.eta;
+        slot = (unsigned)(g - cell * (uint64_t)G.eta);
+    }
+}
+
+template <int KW, int CHUNK, bool PART>
 __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a) {
-    __shared__ InsertSmem<KW> S;
+    __shared__ InsertSmem<KW, CHUNK, PART> S;
+    constexpr int kPack32 = ChunkDims<CHUNK>::kPack32;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = a.K;
     const uint64_t total = a.last - a.first;
@@ -148,8 +186,8 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
     unsigned long long my_windows = 0, my_skipped = 0;
 
     for (uint64_t chunk = blockIdx.x; chunk < a.nchunks; chunk += gridDim.x) {
-        const uint64_t c0 = chunk * (uint64_t)kChunk;
-        const uint64_t e = min(c0 + (uint64_t)(kChunk + K - 1), total);
+        const uint64_t c0 = chunk * (uint64_t)CHUNK;
+        const uint64_t e = min(c0 + (uint64_t)(CHUNK + K - 1), total);
         const unsigned nb = (unsigned)(e - c0);
         const uintptr_t src = (uintptr_t)(a.bases + c0);
         const unsigned head = (unsigned)(src & 15);
@@ -171,6 +209,11 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
         if (tid == 0) {
             S.nvalid = 0;
             S.nfresh = 0;
+            S.nupd = 0;
+        }
+        if (PART && tid < kCoarseBins) {
+            S.hist[tid] = 0;
+            S.fill[tid] = 0;
         }
         __syncthreads();
 
@@ -205,7 +248,7 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
         const uint64_t *brk64 = (const uint64_t *)S.brk;
         const uint64_t maskK = K == 64 ? ~0ull : ((1ull << K) - 1);
         const uint64_t maskK1 = (1ull << (K - 1)) - 1;
-        for (int p0 = 0; p0 < kChunk; p0 += kInsertThreads) {
+        for (int p0 = 0; p0 < CHUNK; p0 += kInsertThreads) {
             unsigned p = (unsigned)(p0 + tid);
             bool window = p + (unsigned)K <= nb && (bits_at(brk64, p + 1) & maskK1) == 0;
             bool valid = window && (bits_at(inv64, p) & maskK) == 0;
@@ -270,13 +313,14 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
             const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
             for (int a0 = 0; a0 < G.nhash; a0 += 4) {
                 uint64_t cell[4], cur[4], prev[4];
-                unsigned sh[4];
+                unsigned sh[4], slot[4];
                 bool use[4], need[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     use[j] = active && (a0 + j < G.nhash);
                     cell[j] = 0;
                     sh[j] = 0;
+                    slot[j] = 0;
                     if (use[j]) {
                         uint64_t h1, h2;
                         if (KW == 1)
@@ -284,11 +328,31 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
                         else
                             murmur16(klo, khi, (uint32_t)(a0 + j), h1, h2);
                         if (a0 + j == 0) table_hash = h2;
-                        locate(G, counter_of(G, h1), cell[j], sh[j]);
+                        locate_slot(G, counter_of(G, h1), cell[j], slot[j]);
+                        sh[j] = slot[j] * (unsigned)G.alpha;
                     }
                 }
                 if (KW == 1 && a0 == 0 && active)
                     table_first = load_hint(a.table + __umul64hi(table_hash, a.cap), pol_stream);
+                if (PART) {
+                    // stage one 32-bit code per increment: coarse region (6 bits),
+                    // cell within the region (20 bits), counter within the cell
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const unsigned bal = __ballot_sync(0xffffffffu, use[j]);
+                        unsigned base = 0;
+                        if (lane == 0 && bal) base = atomicAdd(&S.nupd, (unsigned)__popc(bal));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (use[j]) {
+                            const unsigned bin = (unsigned)(cell[j] >> a.coarse_shift);
+                            const uint32_t code = (bin << 26) |
+                                ((uint32_t)(cell[j] & ((1ull << a.coarse_shift) - 1)) << 6) | slot[j];
+                            S.staged[base + __popc(bal & ((1u << lane) - 1))] = code;
+                            atomicAdd(&S.hist[bin], 1u);
+                        }
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (use[j]) cur[j] = load_hint(G.cells + cell[j], pol_keep);
@@ -322,6 +386,49 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a)
             }
         }
         __syncthreads();
+
+        if (PART) {
+            // 4b. counting sort of the increment codes by coarse region, one
+            //     cursor atomic per region, coalesced runs into the regions
+            const unsigned nupd = S.nupd;
+            if (tid < kCoarseBins) {
+                unsigned pre = 0;
+                for (int b = 0; b < tid; ++b) pre += S.hist[b];
+                S.start[tid] = pre;
+                const unsigned n = S.hist[tid];
+                unsigned long long b0 = ~0ull;
+                if (n) {
+                    b0 = atomicAdd(a.coarse_cursor + tid, (unsigned long long)n);
+                    if (b0 + n > a.coarse_cap)
+                        b0 = ~0ull;   // region full: these go to the global fallback
+                    else
+                        atomicAdd(a.coarse_written + tid, (unsigned long long)n);
+                }
+                S.base[tid] = b0;
+            }
+            __syncthreads();
+            for (unsigned i = tid; i < nupd; i += kInsertThreads) {
+                const uint32_t code = S.staged[i];
+                const unsigned bin = code >> 26;
+                S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = code;
+            }
+            __syncthreads();
+            for (unsigned i = tid; i < nupd; i += kInsertThreads) {
+                const uint32_t code = S.sorted[i];
+                const unsigned bin = code >> 26;
+                const unsigned long long b0 = S.base[bin];
+                if (b0 != ~0ull) {
+                    a.coarse[(uint64_t)bin * a.coarse_cap + b0 + (i - S.start[bin])] = code;
+                } else {
+                    const uint64_t cell = ((uint64_t)bin << a.coarse_shift) |
+                                          ((code >> 6) & ((1u << a.coarse_shift) - 1));
+                    const unsigned shift = (code & 63u) * (unsigned)G.alpha;
+                    sat_increment(G.cells, cell, shift, G.maxc, load_cg(G.cells + cell),
+                                  &a.ctr->error);
+                }
+            }
+            __syncthreads();
+        }
 
         // 5. append this chunk's new keys to the distinct list
         const unsigned nfresh = S.nfresh;
@@ -378,12 +485,12 @@ __global__ void window_bound_kernel(const uint64_t *offsets, uint64_t nreads, in
     }
 }
 
-// first_read[c] = smallest r in [0, nreads] with offsets[r] - first >= c * kChunk.
+// first_read[c] = smallest r in [0, nreads] with offsets[r] - first >= c * chunk.
 __global__ void first_read_kernel(const uint64_t *offsets, uint64_t nreads, uint64_t first,
-                                  uint64_t nchunks, uint32_t *first_read) {
+                                  uint64_t nchunks, uint64_t chunk, uint32_t *first_read) {
     uint64_t c = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
     if (c >= nchunks) return;
-    const uint64_t target = first + c * (uint64_t)kChunk;
+    const uint64_t target = first + c * chunk;
     uint64_t lo = 0, hi = nreads;   // answer in [lo, hi]
     while (lo < hi) {
         uint64_t mid = lo + (hi - lo) / 2;
@@ -434,12 +541,120 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
     }
 }
 
+// Split each coarse region's increment codes into slices of 2^kSliceShift
+// cells.  Block (x, y) takes tile x of coarse region y.
+__global__ void __launch_bounds__(kSortThreads) repartition_kernel(PartArgs p) {
+    __shared__ uint32_t staged[kRepartTile], sorted[kRepartTile];
+    __shared__ unsigned hist[kCoarseBins], start[kCoarseBins], fill[kCoarseBins];
+    __shared__ unsigned long long base[kCoarseBins];
+    const unsigned b = blockIdx.y, tid = threadIdx.x;
+    const uint64_t n = p.coarse_written[b];
+    const uint64_t t0 = (uint64_t)blockIdx.x * kRepartTile;
+    if (t0 >= n) return;
+    const unsigned cnt = (unsigned)min((uint64_t)kRepartTile, n - t0);
+    const unsigned fpc = 1u << (p.coarse_shift - kSliceShift);   // slices per coarse region
+    const uint32_t cmask = (1u << p.coarse_shift) - 1;
+    if (tid < kCoarseBins) {
+        hist[tid] = 0;
+        fill[tid] = 0;
+    }
+    __syncthreads();
+    const uint32_t *src = p.coarse + (uint64_t)b * p.coarse_cap + t0;
+    for (unsigned i = tid; i < cnt; i += kSortThreads) {
+        const uint32_t code = src[i];
+        staged[i] = code;
+        atomicAdd(&hist[((code >> 6) & cmask) >> kSliceShift], 1u);
+    }
+    __syncthreads();
+    if (tid < fpc) {
+        unsigned pre = 0;
+        for (unsigned f = 0; f < tid; ++f) pre += hist[f];
+        start[tid] = pre;
+        const unsigned m = hist[tid];
+        unsigned long long b0 = ~0ull;
+        if (m) {
+            const uint64_t F = (uint64_t)b * fpc + tid;
+            b0 = atomicAdd(p.fine_cursor + F, (unsigned long long)m);
+            if (b0 + m > p.fine_cap)
+                b0 = ~0ull;
+            else
+                atomicAdd(p.fine_written + F, (unsigned long long)m);
+        }
+        base[tid] = b0;
+    }
+    __syncthreads();
+    for (unsigned i = tid; i < cnt; i += kSortThreads) {
+        const uint32_t code = staged[i];
+        const unsigned f = ((code >> 6) & cmask) >> kSliceShift;
+        sorted[start[f] + atomicAdd(&fill[f], 1u)] = code;
+    }
+    __syncthreads();
+    const uint32_t smask = (1u << kSliceShift) - 1;
+    for (unsigned i = tid; i < cnt; i += kSortThreads) {
+        const uint32_t code = sorted[i];
+        const uint32_t word = (code >> 6) & cmask;
+        const unsigned f = word >> kSliceShift;
+        const unsigned long long b0 = base[f];
+        if (b0 != ~0ull) {
+            const uint64_t F = (uint64_t)b * fpc + f;
+            p.fine[F * p.fine_cap + b0 + (i - start[f])] = ((word & smask) << 6) | (code & 63u);
+        } else {
+            const uint64_t cell = ((uint64_t)b << p.coarse_shift) | word;
+            sat_increment(p.G.cells, cell, (code & 63u) * (unsigned)p.G.alpha, p.G.maxc,
+                          load_cg(p.G.cells + cell), &p.ctr->error);
+        }
+    }
+}
+
+// One slice of 2^slice_shift cells per block: load it into shared memory,
+// apply its increment codes with shared-memory compare-and-swap (saturating
+// at 2^alpha - 1), write it back.
+__global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
+    extern __shared__ unsigned long long cells_s[];
+    const uint64_t s = blockIdx.x;
+    const uint64_t w0 = s << p.slice_shift;
+    const uint64_t slice = 1ull << p.slice_shift;
+    const unsigned nw = (unsigned)min(slice, p.G.words - w0);
+    for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) cells_s[i] = p.G.cells[w0 + i];
+    __syncthreads();
+    const uint64_t n = p.written[s];
+    const uint32_t *src = p.codes + s * p.cap;
+    const uint32_t wmask = (uint32_t)(slice - 1);
+    const uint64_t maxc = p.G.maxc;
+    for (uint64_t i = threadIdx.x; i < n; i += kApplyThreads) {
+        const uint32_t code = src[i];
+        const unsigned w = (code >> 6) & wmask;
+        const unsigned shift = (code & 63u) * (unsigned)p.G.alpha;
+        unsigned long long old = cells_s[w];
+        for (uint32_t it = 0;; ++it) {
+            if (((old >> shift) & maxc) == maxc) break;
+            const unsigned long long prev = atomicCAS(cells_s + w, old, old + (1ull << shift));
+            if (prev == old) break;
+            old = prev;
+            if (it >= kCasLimit) {
+                atomicOr(&p.ctr->error, kErrCasLimit);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) p.G.cells[w0 + i] = cells_s[i];
+}
+
 }  // namespace
 
-int insert_blocks_per_sm() {
-    int n1 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, insert_kernel<1>, kInsertThreads, 0);
-    return n1 > 0 ? n1 : 1;
+int insert_blocks_per_sm(int kw, bool partitioned) {
+    int n = 0;
+    if (partitioned)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_kernel<1, kPartChunk, true>,
+                                                      kInsertThreads, 0);
+    else if (kw == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_kernel<1, kChunk, false>,
+                                                      kInsertThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_kernel<2, kChunk, false>,
+                                                      kInsertThreads, 0);
+    return n > 0 ? n : 1;
 }
 
 cudaError_t launch_window_bound(const uint64_t *offsets, uint64_t nreads, int K, DevCounters *ctr,
@@ -452,20 +667,40 @@ cudaError_t launch_window_bound(const uint64_t *offsets, uint64_t nreads, int K,
 }
 
 cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t first,
-                              uint64_t nchunks, uint32_t *first_read, cudaStream_t s) {
+                              uint64_t nchunks, uint64_t chunk, uint32_t *first_read,
+                              cudaStream_t s) {
     if (nchunks == 0) return cudaSuccess;
     first_read_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, s>>>(offsets, nreads, first,
-                                                                         nchunks, first_read);
+                                                                         nchunks, chunk, first_read);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s) {
+    const uint64_t tiles = (p.coarse_cap + kRepartTile - 1) / kRepartTile;
+    if (tiles == 0) return cudaSuccess;
+    repartition_kernel<<<dim3((unsigned)tiles, kCoarseBins), kSortThreads, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
+    if (nslices == 0) return cudaSuccess;
+    const size_t smem = (size_t)8 << p.slice_shift;
+    cudaError_t e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(8 << kSliceShift));
+    if (e != cudaSuccess) return e;
+    apply_kernel<<<(unsigned)nslices, kApplyThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s) {
     if (a.nchunks == 0) return cudaSuccess;
     uint64_t g = a.nchunks < (uint64_t)grid ? a.nchunks : (uint64_t)grid;
-    if (a.K <= 32)
-        insert_kernel<1><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
+    if (a.part)
+        insert_kernel<1, kPartChunk, true><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
+    else if (a.K <= 32)
+        insert_kernel<1, kChunk, false><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
     else
-        insert_kernel<2><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
+        insert_kernel<2, kChunk, false><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

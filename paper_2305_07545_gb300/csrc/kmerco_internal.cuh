@@ -12,6 +12,13 @@ namespace countbf {
 constexpr uint64_t kEmptyKey = ~0ull;      // empty slot of the distinct-key set;
                                            // no canonical key is all ones
 constexpr int kChunk = 2048;               // window starts per insert work unit
+constexpr int kPartChunk = 1024;           // the same in the partitioned update design
+constexpr int kPartMaxHash = 4;            // hashes the partitioned design stages per window
+constexpr int kCoarseBins = 64;            // coarse countBF regions of the partitioned design
+constexpr int kSliceShift = 14;            // 2^14 cells (128 KiB) per shared-memory slice
+constexpr int kMaxCoarseShift = 20;        // cell-in-region bits of an increment code
+constexpr int kRepartTile = 4096;          // codes per repartition block
+constexpr int kApplyThreads = 1024;
 constexpr int kInsertThreads = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
@@ -185,14 +192,46 @@ struct InsertArgs {
     uint64_t *dlist;             // distinct keys in arrival order
     uint64_t dlist_cap;
     DevCounters *ctr;
+    // partitioned update design (part != 0)
+    int part;
+    int coarse_shift;                      // coarse region = cell >> coarse_shift
+    uint32_t *coarse;                      // kCoarseBins regions of coarse_cap codes
+    uint64_t coarse_cap;
+    unsigned long long *coarse_cursor;     // codes reserved per region
+    unsigned long long *coarse_written;    // codes written per region (a prefix)
+};
+
+struct PartArgs {
+    Geometry G;
+    int coarse_shift;
+    const uint32_t *coarse;
+    uint64_t coarse_cap;
+    const unsigned long long *coarse_written;
+    uint32_t *fine;                        // one region of fine_cap codes per slice
+    uint64_t fine_cap;
+    unsigned long long *fine_cursor;
+    unsigned long long *fine_written;
+    DevCounters *ctr;
+};
+
+struct ApplyArgs {
+    Geometry G;
+    int slice_shift;                       // cells per slice = 2^slice_shift
+    const uint32_t *codes;                 // one region of cap codes per slice
+    uint64_t cap;
+    const unsigned long long *written;     // codes per slice
+    DevCounters *ctr;
 };
 
 cudaError_t launch_window_bound(const uint64_t *offsets, uint64_t nreads, int K,
                                 DevCounters *ctr, cudaStream_t s);
 cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t first,
-                              uint64_t nchunks, uint32_t *first_read, cudaStream_t s);
+                              uint64_t nchunks, uint64_t chunk, uint32_t *first_read,
+                              cudaStream_t s);
 cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s);
-int insert_blocks_per_sm();
+int insert_blocks_per_sm(int kw, bool partitioned);
+cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s);
+cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
 // Insert n keys into a distinct set; when dlist is not null, keys new to the
 // set are appended to it (ctr->distinct counts them).
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,

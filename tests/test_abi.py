@@ -67,3 +67,15 @@ def test_python_error_type(lib):
     with pytest.raises(kc.KmercoError) as e:
         kc.kmerco_create(21, 1 << 10, 4, 3, 99)
     assert e.value.status == kc.EINVAL
+
+
+@pytest.mark.parametrize("k,m,nhash", [(33, 1 << 20, 4), (21, 1 << 20, 5), (21, 1 << 33, 4)])
+def test_partitioned_mode_limits(lib, k, m, nhash):
+    # the partitioned update design needs one-word keys, k_h <= 4 and at most
+    # 2^26 cells; asking for it otherwise is rejected before any GPU work
+    with pytest.raises(kc.KmercoError) as e:
+        kc.kmerco_create_ex(k, m, 4, nhash, 3, update_mode=kc.UPDATE_PARTITIONED)
+    assert e.value.status == kc.EINVAL
+    with pytest.raises(kc.KmercoError) as e:
+        kc.kmerco_create_ex(21, 1 << 20, 4, 3, 2, update_mode=3)
+    assert e.value.status == kc.EINVAL

@@ -25,8 +25,9 @@ def _dev(a: np.ndarray):
 
 
 def gpu_run(bases, offsets, K, m, alpha, nhash, tau, device_inputs=True, forward_only=False,
-            batches=None):
-    with kc.CountBF(K, m, alpha, nhash, tau, forward_only=forward_only) as bf:
+            batches=None, update_mode=0):
+    with kc.CountBF(K, m, alpha, nhash, tau, forward_only=forward_only,
+                    update_mode=update_mode) as bf:
         parts = batches or [(bases, offsets)]
         for b, o in parts:
             if device_inputs:
@@ -124,6 +125,35 @@ def test_many_tiny_and_empty_reads():
     g = gpu_run(b, o, 21, 1 << 14, 4, 3, 2)
     ref = check(g, b, o, 21, 4, 3, 2)
     assert ref.n_inserted > 0
+
+
+UPDATE_CASES = [
+    # K, m, alpha, nhash, tau
+    (21, 1 << 12, 4, 4, 2),            # one coarse region per few cells
+    (21, 1 << 20, 4, 3, 2),            # 2^16 cells: slices are the coarse regions
+    (31, 1 << 24, 4, 4, 3),            # 2^20 cells: coarse region == one slice
+    (31, 1 << 25, 4, 4, 3),            # 2^21 cells: coarse regions split into 2 slices
+    (21, 3 * (1 << 23) + 48, 4, 4, 2), # non power-of-two m, partial last slice
+    (17, 12 << 20, 5, 4, 3),           # eta = 12
+    (25, 1 << 24, 8, 2, 3),            # eta = 8, k_h = 2
+]
+
+
+@pytest.mark.parametrize("mode", [kc.UPDATE_ATOMIC, kc.UPDATE_PARTITIONED])
+@pytest.mark.parametrize("K,m,alpha,nhash,tau", UPDATE_CASES)
+def test_both_update_designs(mode, K, m, alpha, nhash, tau):
+    b, o = readsim.scaled("tiny", 1500, seed_offset=K + alpha).generate()
+    g = gpu_run(b, o, K, m, alpha, nhash, tau, update_mode=mode)
+    check(g, b, o, K, alpha, nhash, tau)
+
+
+def test_partitioned_overflow_falls_back_exactly():
+    # one read repeated: its few cells receive almost every increment, so the
+    # coarse and slice buffers overflow and the global fallback takes over
+    b, o = readsim.from_strings(["ACGTTGCATTGACCAGTAGGACCATTAGCAGGATTACA"] * 4000)
+    for m in (1 << 20, 1 << 25):
+        g = gpu_run(b, o, 21, m, 8, 4, 3, update_mode=kc.UPDATE_PARTITIONED)
+        check(g, b, o, 21, 8, 4, 3)
 
 
 def test_repeated_read_contention():
