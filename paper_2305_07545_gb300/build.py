@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libkmerco.so")
-SOURCES = ["kmerco_api.cu", "kmerco_insert.cu", "kmerco_classify.cu", "kmerco_noalloc.cu"]
+SOURCES = ["kmerco_api.cu", "kmerco_insert.cu", "kmerco_classify.cu",
+           "kmerco_noalloc.cu"]
 DEPS = ["kmerco_internal.cuh", os.path.join("..", "..", "include", "kmerco.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v"]

@@ -61,6 +61,11 @@ struct kmerco {
     uint64_t fine_alloc;
     unsigned long long *part_ctr;   // region cursors and written counts
     uint64_t part_ctr_alloc;
+    unsigned long long *bucket_scratch;   // classify: bucket histogram, starts, cursors
+    uint64_t bucket_scratch_cap;
+    unsigned long long *bucket_host;      // pinned copy of the bucket starts
+    unsigned short *hist_partial;         // per-block partial histograms
+    uint64_t hist_partial_cap;
 };
 
 namespace {
@@ -216,9 +221,10 @@ bool use_partitioned(const kmerco_t *h) {
     return able && h->G.words >= (1ull << 17);   // smaller countBFs stay L2-resident
 }
 
+// Smallest l with 2^l >= x (64 for x above 2^63).
 int ceil_log2(uint64_t x) {
     int l = 0;
-    while ((1ull << l) < x) ++l;
+    while (l < 64 && (1ull << l) < x) ++l;
     return l;
 }
 
@@ -357,6 +363,9 @@ void kmerco_destroy(kmerco_t *h) {
         dev_free(h, h->coarse, h->coarse_alloc * 4);
         dev_free(h, h->fine, h->fine_alloc * 4);
         dev_free(h, h->part_ctr, h->part_ctr_alloc * 8);
+        dev_free(h, h->bucket_scratch, h->bucket_scratch_cap * 8);
+        dev_free(h, h->hist_partial, h->hist_partial_cap * 2);
+        if (h->bucket_host) cudaFreeHost(h->bucket_host);
         if (h->ctr_host) cudaFreeHost(h->ctr_host);
         for (int i = 0; i < 4; ++i)
             if (h->ev[i]) cudaEventDestroy(h->ev[i]);
@@ -441,9 +450,9 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
         slice_shift = repart ? kSliceShift : coarse_shift;
         nslices = (W + (1ull << slice_shift) - 1) >> slice_shift;
         coarse_cap = U / kCoarseBins;
-        coarse_cap += coarse_cap / 6 + 4096;
+        coarse_cap = (coarse_cap + coarse_cap / 6 + 4096 + 3) & ~3ull;   // multiple of 4 codes
         fine_cap = repart ? U / nslices : 0;
-        fine_cap += fine_cap / 5 + 1024;
+        fine_cap = (fine_cap + fine_cap / 5 + 1024 + 3) & ~3ull;
         if (U > (1ull << 31) ||
             ensure(h, &h->coarse, &h->coarse_alloc, kCoarseBins * coarse_cap) != KMERCO_OK ||
             (repart && ensure(h, &h->fine, &h->fine_alloc, nslices * fine_cap) != KMERCO_OK) ||
@@ -525,7 +534,7 @@ int kmerco_classify(kmerco_t *h) {
     KM_TRY(read_counters(h));
     KM_TRY(device_error_status(h->ctr_host->error));
     const uint64_t D = h->ctr_host->distinct;
-    if (D >= 0xFFFFFFFFull) return KMERCO_ENOMEM;   // radix tiles index keys with 32 bits
+    if (D >= 0xFFFFFFFFull) return KMERCO_ENOMEM;   // sort tiles index keys with 32 bits
     const int kw = h->kw;
     KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, D * kw));
     KM_TRY(ensure(h, &h->alt1, &h->alt1_cap, D * kw));
@@ -534,13 +543,105 @@ int kmerco_classify(kmerco_t *h) {
     KM_TRY(ensure(h, &h->sort_scratch, &h->sort_scratch_cap, sort_scratch_words(D, kw)));
     KM_TRY(ensure(h, &h->split_scratch, &h->split_scratch_cap, split_scratch_words(D)));
     KM_CUDA(cudaEventRecord(h->ev[2], h->stream));
-    const uint64_t *sorted = h->dlist;
-    KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D, kw, 2 * h->K, h->sort_scratch, &sorted,
-                       h->stream));
+    const uint64_t *const distinct_in = h->dlist;   // arrival order; left unchanged
+    const uint64_t *sorted = distinct_in;
+    const int bits = 2 * h->K;
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    if (kw == 1 && bits >= kHistBits + 8 && D > 1 &&
+        D <= (uint64_t)kHistBins * (kBucketCap / 4)) {
+        // Bucket sort: histogram of the top kHistBits key bits, adjacent bins
+        // merged into super-buckets of at most kBucketCap keys, each sorted in
+        // shared memory.  A single bin above kBucketCap is radix sorted.
+        const int shift = bits - kHistBits;
+        // device and pinned layout: hist u32[B] | map u32[B] | start u64[B+1] |
+        // lo u64[B] | rsh i32[B] (| cursor u64[B] on the device only)
+        const uint64_t words = 4 * (uint64_t)kHistBins + 1 + kHistBins / 2;
+        KM_TRY(ensure(h, &h->bucket_scratch, &h->bucket_scratch_cap, words + kHistBins));
+        unsigned *d_hist = (unsigned *)h->bucket_scratch;
+        unsigned *d_map = d_hist + kHistBins;
+        unsigned long long *d_start = h->bucket_scratch + kHistBins;
+        unsigned long long *d_lo = d_start + kHistBins + 1;
+        int *d_rsh = (int *)(d_lo + kHistBins);
+        unsigned long long *d_cursor = (unsigned long long *)(d_rsh + kHistBins);
+        if (!h->bucket_host &&
+            cudaMallocHost((void **)&h->bucket_host, words * sizeof(unsigned long long)) != cudaSuccess) {
+            h->bucket_host = nullptr;
+            return KMERCO_ENOMEM;
+        }
+        unsigned *hist = (unsigned *)h->bucket_host, *map = hist + kHistBins;
+        unsigned long long *start = h->bucket_host + kHistBins;
+        unsigned long long *lo = start + kHistBins + 1;
+        int *rsh = (int *)(lo + kHistBins);
+        const uint64_t hb = bucket_hist_blocks(D);
+        KM_TRY(ensure(h, &h->hist_partial, &h->hist_partial_cap, hb * kHistBins));
+        KM_CUDA(bucket_histogram(distinct_in, D, shift, h->hist_partial, d_hist, h->stream));
+        KM_CUDA(cudaMemcpyAsync(hist, d_hist, kHistBins * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                h->stream));
+        KM_CUDA(cudaStreamSynchronize(h->stream));
+        // greedy merge of adjacent bins into super-buckets of <= kBucketCap keys;
+        // super-bucket b covers bins [first, last]: key range lo .. (last+1) << shift
+        unsigned nsuper = 0;
+        unsigned long long cur = 0;
+        int first = 0;
+        start[0] = 0;
+        auto close = [&](int last) {
+            lo[nsuper] = (unsigned long long)first << shift;
+            // key range of the super-bucket is (last - first + 1) << shift, which
+            // needs up to 64 + log2(bins) bits; map it onto 2^12 sub-bins
+            int r = ceil_log2((uint64_t)(last - first + 1)) + shift - 12;
+            if (r > 63) r = 63;
+            rsh[nsuper] = r < 0 ? 0 : r;
+            start[nsuper + 1] = start[nsuper] + cur;
+            ++nsuper;
+        };
+        for (int i = 0; i < kHistBins; ++i) {
+            if (cur > 0 && cur + hist[i] > (unsigned long long)kBucketCap) {
+                close(i - 1);
+                cur = 0;
+                first = i;
+            }
+            map[i] = nsuper;
+            cur += hist[i];
+        }
+        close(kHistBins - 1);
+        if (nsuper > (unsigned)kMaxSuper) {
+            // too many super-buckets for the scatter's shared counters
+            KM_CUDA(radix_sort(distinct_in, h->alt0, h->alt1, D, kw, bits, h->sort_scratch,
+                               &sorted, h->stream));
+            h->launches += 3 * (uint64_t)passes;
+            goto sorted_done;
+        }
+        KM_CUDA(cudaMemcpyAsync(d_map, map, kHistBins * sizeof(unsigned), cudaMemcpyHostToDevice,
+                                h->stream));
+        KM_CUDA(cudaMemcpyAsync(d_start, start, (nsuper + 1) * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, h->stream));
+        KM_CUDA(cudaMemcpyAsync(d_lo, lo, nsuper * sizeof(unsigned long long),
+                                cudaMemcpyHostToDevice, h->stream));
+        KM_CUDA(cudaMemcpyAsync(d_rsh, rsh, nsuper * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        KM_CUDA(bucket_place_and_sort(distinct_in, h->alt0, D, shift, d_map, nsuper, d_start, d_lo,
+                                      d_rsh, d_cursor, h->stream));
+        h->launches += 4;
+        sorted = h->alt0;
+        for (unsigned b = 0; b < nsuper; ++b) {
+            const uint64_t n_b = start[b + 1] - start[b];
+            if (n_b <= (uint64_t)kBucketCap) continue;
+            uint64_t *range = h->alt0 + start[b];
+            const uint64_t *res = range;
+            KM_CUDA(radix_sort(range, h->alt1, range, n_b, 1, bits, h->sort_scratch, &res,
+                               h->stream));
+            h->launches += 3 * (uint64_t)passes;
+            if (res != range)
+                KM_CUDA(cudaMemcpyAsync(range, res, n_b * 8, cudaMemcpyDeviceToDevice, h->stream));
+        }
+    } else {
+        KM_CUDA(radix_sort(distinct_in, h->alt0, h->alt1, D, kw, bits, h->sort_scratch,
+                           &sorted, h->stream));
+        if (D > 1) h->launches += 3 * (uint64_t)passes;
+    }
+sorted_done:
     KM_CUDA(launch_query(sorted, D, kw, h->K, h->G, h->est, h->stream));
     KM_CUDA(launch_split(sorted, h->est, D, kw, h->tau, h->split, h->split_scratch, h->ctr,
                          h->stream));
-    if (D > 1) h->launches += 3 * (uint64_t)((2 * h->K + kRadixBits - 1) / kRadixBits);
     if (D > 0) h->launches += 4;   // query + three split kernels
     KM_CUDA(cudaEventRecord(h->ev[3], h->stream));
     KM_TRY(read_counters(h));

@@ -6,6 +6,10 @@
 //    digit counts, one scan per digit across tiles, then a stable scatter
 //    in which each warp ranks equal digits with __match_any_sync and the
 //    tile is reordered in shared memory before coalesced stores.
+//  - bucket_sort (one-word keys): the top 12 of the 2K key bits split the
+//    keys into 4096 buckets in one scatter pass (cursor atomics aggregated
+//    per block), then each bucket is bitonic-sorted in shared memory by one
+//    block.  Buckets too large for shared memory are left to radix_sort.
 //  - query: per key, k_h hashes and the minimum counter, 0 if any is 0.
 //  - split: stable partition on est > tau (trustworthy first).
 //  - merge: counter-wise min(a + b, 2^alpha - 1) of two countBFs.
@@ -41,6 +45,35 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T &total) {
     __syncthreads();
     T before = warp ? warp_sums[warp - 1] : T(0);
     total = warp_sums[kWarps - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+// Exclusive scan across a block of NT threads.
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan_n(T v, T &total) {
+    __shared__ T wsum[NT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T s = lane < NT / 32 ? wsum[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < NT / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    T before = warp ? wsum[warp - 1] : T(0);
+    total = wsum[NT / 32 - 1];
     __syncthreads();
     return before + x - v;
 }
@@ -299,6 +332,178 @@ __global__ void count_saturated_kernel(Geometry G, DevCounters *ctr) {
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(&ctr->saturated, c);
 }
 
+// ---------------------------------------------------------------- bucket sort
+// Partial histograms of key >> shift over kHistBins bins: block b counts the
+// keys of its tile (at most 65,535) in 16-bit shared counters and writes them
+// to partial[b * kHistBins ...].
+__global__ void __launch_bounds__(512) bucket_hist_kernel(const uint64_t *keys, uint64_t n,
+                                                          int shift, unsigned short *partial) {
+    extern __shared__ unsigned hh32[];   // kHistBins 16-bit counters, two per word
+    unsigned short *hh = (unsigned short *)hh32;
+    for (unsigned i = threadIdx.x; i < kHistBins / 2; i += blockDim.x) hh32[i] = 0;
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)blockIdx.x * kHistTile;
+    const unsigned cnt = (unsigned)min((uint64_t)kHistTile, n - t0);
+    for (unsigned i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const unsigned b = (unsigned)(keys[t0 + i] >> shift);
+        atomicAdd(&hh32[b >> 1], 1u << (16 * (b & 1)));   // a 16-bit lane never exceeds 65,535
+    }
+    __syncthreads();
+    unsigned short *out = partial + (uint64_t)blockIdx.x * kHistBins;
+    for (unsigned i = threadIdx.x; i < kHistBins; i += blockDim.x) out[i] = hh[i];
+}
+
+// hist[i] = sum over blocks of partial[b][i].
+__global__ void bucket_hist_reduce_kernel(const unsigned short *partial, unsigned nblocks,
+                                          unsigned *hist) {
+    const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kHistBins) return;
+    unsigned s = 0;
+    for (unsigned b = 0; b < nblocks; ++b) s += partial[(uint64_t)b * kHistBins + i];
+    hist[i] = s;
+}
+
+// One tile of keys per block: count per super-bucket, reserve each
+// super-bucket's run with one global atomic, then place the keys (order
+// within a super-bucket is arbitrary; each is sorted afterwards).  Keys are
+// read eight per thread at a time so that the loads overlap.
+__global__ void __launch_bounds__(256) bucket_scatter_kernel(const uint64_t *keys, uint64_t n,
+                                                             int shift, const unsigned *map,
+                                                             unsigned nsuper,
+                                                             unsigned long long *cursor,
+                                                             uint64_t *out) {
+    extern __shared__ unsigned sc[];
+    unsigned *h = sc, *base = sc + nsuper;
+    const uint64_t t0 = (uint64_t)blockIdx.x * kScatterTile;
+    const unsigned cnt = (unsigned)min((uint64_t)kScatterTile, n - t0);
+    for (unsigned i = threadIdx.x; i < nsuper; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    constexpr unsigned kB = 8, kStride = 256;
+    for (unsigned i0 = 0; i0 < cnt; i0 += kB * kStride) {
+        uint64_t k[kB];
+#pragma unroll
+        for (unsigned q = 0; q < kB; ++q) {
+            const unsigned i = i0 + q * kStride + threadIdx.x;
+            k[q] = i < cnt ? __ldg(keys + t0 + i) : 0;
+        }
+#pragma unroll
+        for (unsigned q = 0; q < kB; ++q)
+            if (i0 + q * kStride + threadIdx.x < cnt) atomicAdd(&h[__ldg(map + (k[q] >> shift))], 1u);
+    }
+    __syncthreads();
+    for (unsigned b = threadIdx.x; b < nsuper; b += blockDim.x) {
+        if (h[b]) base[b] = (unsigned)atomicAdd(cursor + b, (unsigned long long)h[b]);
+        h[b] = 0;
+    }
+    __syncthreads();
+    for (unsigned i0 = 0; i0 < cnt; i0 += kB * kStride) {
+        uint64_t k[kB];
+#pragma unroll
+        for (unsigned q = 0; q < kB; ++q) {
+            const unsigned i = i0 + q * kStride + threadIdx.x;
+            k[q] = i < cnt ? __ldg(keys + t0 + i) : 0;
+        }
+#pragma unroll
+        for (unsigned q = 0; q < kB; ++q) {
+            if (i0 + q * kStride + threadIdx.x < cnt) {
+                const unsigned b = __ldg(map + (k[q] >> shift));
+                out[base[b] + atomicAdd(&h[b], 1u)] = k[q];
+            }
+        }
+    }
+}
+
+// Sort of one super-bucket (at most kBucketCap keys) in shared memory: a
+// counting sort on the 12 bits below the super-bucket's common range
+// (sub = (key - lo) >> rsh), then an insertion sort of each small
+// sub-bucket.  When the keys cluster so that a sub-bucket holds more than
+// kSubMax keys, the block bitonic-sorts the whole super-bucket instead.
+__global__ void __launch_bounds__(kBucketThreads) bucket_sort_kernel(
+    uint64_t *data, const unsigned long long *start, const unsigned long long *lo,
+    const int *rsh) {
+    extern __shared__ unsigned long long sm[];
+    unsigned long long *A = sm, *B = sm + kBucketCap;
+    unsigned *hist = (unsigned *)(sm + 2 * kBucketCap);
+    unsigned *st = hist + kSubBins, *fill = st + kSubBins;
+    __shared__ unsigned maxsub;
+    const unsigned long long s0 = start[blockIdx.x];
+    const unsigned n = (unsigned)(start[blockIdx.x + 1] - s0);
+    if (n <= 1 || n > (unsigned)kBucketCap) return;
+    const unsigned long long base = lo[blockIdx.x];
+    const int r = rsh[blockIdx.x];
+    const unsigned tid = threadIdx.x;
+    for (unsigned i = tid; i < kSubBins; i += kBucketThreads) hist[i] = 0;
+    if (tid == 0) maxsub = 0;
+    __syncthreads();
+    for (unsigned i = tid; i < n; i += kBucketThreads) {
+        const unsigned long long k = data[s0 + i];
+        A[i] = k;
+        atomicAdd(&hist[min((unsigned)((k - base) >> r), (unsigned)kSubBins - 1)], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of the kSubBins counts: 4 per thread
+    {
+        unsigned v[4], sum = 0, mx = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = hist[tid * 4 + j];
+            sum += v[j];
+            mx = max(mx, v[j]);
+        }
+        unsigned tot;
+        unsigned pre = block_exclusive_scan_n<unsigned, kBucketThreads>(sum, tot);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            st[tid * 4 + j] = pre;
+            fill[tid * 4 + j] = pre;
+            pre += v[j];
+        }
+        atomicMax(&maxsub, mx);
+    }
+    __syncthreads();
+    for (unsigned i = tid; i < n; i += kBucketThreads) {
+        const unsigned long long k = A[i];
+        B[atomicAdd(&fill[min((unsigned)((k - base) >> r), (unsigned)kSubBins - 1)], 1u)] = k;
+    }
+    __syncthreads();
+    if (maxsub <= (unsigned)kSubMax) {
+        for (unsigned b = tid; b < kSubBins; b += kBucketThreads) {
+            const unsigned a0 = st[b], m = hist[b];
+            for (unsigned i = 1; i < m; ++i) {
+                const unsigned long long k = B[a0 + i];
+                unsigned j = i;
+                while (j > 0 && B[a0 + j - 1] > k) {
+                    B[a0 + j] = B[a0 + j - 1];
+                    --j;
+                }
+                B[a0 + j] = k;
+            }
+        }
+    } else {
+        unsigned P = 2;
+        while (P < n) P <<= 1;
+        for (unsigned i = n + tid; i < P; i += kBucketThreads) B[i] = ~0ull;
+        __syncthreads();
+        for (unsigned k = 2; k <= P; k <<= 1) {
+            for (unsigned j = k >> 1; j > 0; j >>= 1) {
+                for (unsigned i = tid; i < P; i += kBucketThreads) {
+                    const unsigned ixj = i ^ j;
+                    if (ixj > i) {
+                        const unsigned long long a = B[i], b = B[ixj];
+                        if ((a > b) == ((i & k) == 0)) {
+                            B[i] = b;
+                            B[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    for (unsigned i = tid; i < n; i += kBucketThreads) data[s0 + i] = B[i];
+}
+
 uint32_t sort_tiles(uint64_t n, int kw) {
     const uint64_t t = kw == 1 ? (uint64_t)tile_keys<1>() : (uint64_t)tile_keys<2>();
     return (uint32_t)((n + t - 1) / t);
@@ -311,6 +516,39 @@ unsigned grid_for(uint64_t n, unsigned threads, unsigned cap) {
 }
 
 }  // namespace
+
+uint64_t bucket_hist_blocks(uint64_t n) { return (n + kHistTile - 1) / kHistTile; }
+
+cudaError_t bucket_histogram(const uint64_t *keys, uint64_t n, int shift, unsigned short *partial,
+                             unsigned *hist, cudaStream_t s) {
+    const uint64_t nb = bucket_hist_blocks(n);
+    const int smem = kHistBins * 2;
+    cudaError_t e = cudaFuncSetAttribute(bucket_hist_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    bucket_hist_kernel<<<(unsigned)nb, 512, smem, s>>>(keys, n, shift, partial);
+    bucket_hist_reduce_kernel<<<(kHistBins + 255) / 256, 256, 0, s>>>(partial, (unsigned)nb, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t bucket_place_and_sort(const uint64_t *in, uint64_t *out, uint64_t n, int shift,
+                                  const unsigned *map, unsigned nsuper,
+                                  const unsigned long long *start, const unsigned long long *lo,
+                                  const int *rsh, unsigned long long *cursor, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(cursor, start, nsuper * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    const int smem = (int)(2 * nsuper * sizeof(unsigned));
+    e = cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    bucket_scatter_kernel<<<(unsigned)((n + kScatterTile - 1) / kScatterTile), 256, smem, s>>>(
+        in, n, shift, map, nsuper, cursor, out);
+    const int ssmem = 2 * kBucketCap * 8 + 3 * kSubBins * 4;
+    e = cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem);
+    if (e != cudaSuccess) return e;
+    bucket_sort_kernel<<<nsuper, kBucketThreads, ssmem, s>>>(out, start, lo, rsh);
+    return cudaGetLastError();
+}
 
 uint64_t sort_scratch_words(uint64_t n, int kw) {
     return (uint64_t)kRadixBins * sort_tiles(n, kw) + kRadixBins;

@@ -543,8 +543,9 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
 
 // Split each coarse region's increment codes into slices of 2^kSliceShift
 // cells.  Block (x, y) takes tile x of coarse region y.
-__global__ void __launch_bounds__(kSortThreads) repartition_kernel(PartArgs p) {
-    __shared__ uint32_t staged[kRepartTile], sorted[kRepartTile];
+__global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p) {
+    extern __shared__ uint32_t rp_smem[];
+    uint32_t *staged = rp_smem, *sorted = rp_smem + kRepartTile;
     __shared__ unsigned hist[kCoarseBins], start[kCoarseBins], fill[kCoarseBins];
     __shared__ unsigned long long base[kCoarseBins];
     const unsigned b = blockIdx.y, tid = threadIdx.x;
@@ -559,11 +560,34 @@ __global__ void __launch_bounds__(kSortThreads) repartition_kernel(PartArgs p) {
         fill[tid] = 0;
     }
     __syncthreads();
+    // 16 codes per thread, all loads issued before use (the region is 16-byte
+    // aligned: coarse_cap is a multiple of 4 and t0 of kRepartTile)
     const uint32_t *src = p.coarse + (uint64_t)b * p.coarse_cap + t0;
-    for (unsigned i = tid; i < cnt; i += kSortThreads) {
-        const uint32_t code = src[i];
-        staged[i] = code;
-        atomicAdd(&hist[((code >> 6) & cmask) >> kSliceShift], 1u);
+    uint32_t c16[16];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned i = 4 * (tid + j * kRepartThreads);
+        if (i + 4 <= cnt) {
+            const uint4 v = __ldcs((const uint4 *)(src + i));
+            c16[4 * j] = v.x;
+            c16[4 * j + 1] = v.y;
+            c16[4 * j + 2] = v.z;
+            c16[4 * j + 3] = v.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c16[4 * j + q] = i + q < cnt ? src[i + q] : 0u;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned i = 4 * (tid + j * kRepartThreads);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i + q < cnt) {
+                staged[i + q] = c16[4 * j + q];
+                atomicAdd(&hist[((c16[4 * j + q] >> 6) & cmask) >> kSliceShift], 1u);
+            }
+        }
     }
     __syncthreads();
     if (tid < fpc) {
@@ -583,14 +607,14 @@ __global__ void __launch_bounds__(kSortThreads) repartition_kernel(PartArgs p) {
         base[tid] = b0;
     }
     __syncthreads();
-    for (unsigned i = tid; i < cnt; i += kSortThreads) {
+    for (unsigned i = tid; i < cnt; i += kRepartThreads) {
         const uint32_t code = staged[i];
         const unsigned f = ((code >> 6) & cmask) >> kSliceShift;
         sorted[start[f] + atomicAdd(&fill[f], 1u)] = code;
     }
     __syncthreads();
     const uint32_t smask = (1u << kSliceShift) - 1;
-    for (unsigned i = tid; i < cnt; i += kSortThreads) {
+    for (unsigned i = tid; i < cnt; i += kRepartThreads) {
         const uint32_t code = sorted[i];
         const uint32_t word = (code >> 6) & cmask;
         const unsigned f = word >> kSliceShift;
@@ -618,22 +642,49 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
     for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) cells_s[i] = p.G.cells[w0 + i];
     __syncthreads();
     const uint64_t n = p.written[s];
-    const uint32_t *src = p.codes + s * p.cap;
+    const uint32_t *src = p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
     const uint32_t wmask = (uint32_t)(slice - 1);
     const uint64_t maxc = p.G.maxc;
-    for (uint64_t i = threadIdx.x; i < n; i += kApplyThreads) {
-        const uint32_t code = src[i];
-        const unsigned w = (code >> 6) & wmask;
-        const unsigned shift = (code & 63u) * (unsigned)p.G.alpha;
-        unsigned long long old = cells_s[w];
-        for (uint32_t it = 0;; ++it) {
-            if (((old >> shift) & maxc) == maxc) break;
-            const unsigned long long prev = atomicCAS(cells_s + w, old, old + (1ull << shift));
-            if (prev == old) break;
-            old = prev;
-            if (it >= kCasLimit) {
-                atomicOr(&p.ctr->error, kErrCasLimit);
-                break;
+    const unsigned alpha = (unsigned)p.G.alpha;
+    // eight codes per thread in flight (two 16-byte loads), then their updates
+    constexpr unsigned kStep = kApplyThreads * 8;
+    for (uint64_t i0 = 0; i0 < n; i0 += kStep) {
+        uint32_t code[8];
+        unsigned valid = 0;
+        const uint64_t i = i0 + threadIdx.x * 4ull;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t j = i + (uint64_t)h * kApplyThreads * 4;
+            if (j + 4 <= n) {
+                const uint4 v = __ldcs((const uint4 *)(src + j));
+                code[4 * h] = v.x;
+                code[4 * h + 1] = v.y;
+                code[4 * h + 2] = v.z;
+                code[4 * h + 3] = v.w;
+                valid |= 0xFu << (4 * h);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    code[4 * h + q] = j + q < n ? src[j + q] : 0u;
+                    valid |= (j + q < n ? 1u : 0u) << (4 * h + q);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (!((valid >> q) & 1u)) continue;   // past the end
+            const unsigned w = (code[q] >> 6) & wmask;
+            const unsigned shift = (code[q] & 63u) * alpha;
+            unsigned long long old = cells_s[w];
+            for (uint32_t it = 0;; ++it) {
+                if (((old >> shift) & maxc) == maxc) break;
+                const unsigned long long prev = atomicCAS(cells_s + w, old, old + (1ull << shift));
+                if (prev == old) break;
+                old = prev;
+                if (it >= kCasLimit) {
+                    atomicOr(&p.ctr->error, kErrCasLimit);
+                    break;
+                }
             }
         }
     }
@@ -678,7 +729,11 @@ cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t
 cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s) {
     const uint64_t tiles = (p.coarse_cap + kRepartTile - 1) / kRepartTile;
     if (tiles == 0) return cudaSuccess;
-    repartition_kernel<<<dim3((unsigned)tiles, kCoarseBins), kSortThreads, 0, s>>>(p);
+    const int smem = 2 * kRepartTile * (int)sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(repartition_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    repartition_kernel<<<dim3((unsigned)tiles, kCoarseBins), kRepartThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

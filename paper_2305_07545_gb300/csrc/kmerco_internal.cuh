@@ -17,8 +17,18 @@ constexpr int kPartMaxHash = 4;            // hashes the partitioned design stag
 constexpr int kCoarseBins = 64;            // coarse countBF regions of the partitioned design
 constexpr int kSliceShift = 14;            // 2^14 cells (128 KiB) per shared-memory slice
 constexpr int kMaxCoarseShift = 20;        // cell-in-region bits of an increment code
-constexpr int kRepartTile = 4096;          // codes per repartition block
+constexpr int kRepartTile = 8192;          // codes per repartition block
+constexpr int kRepartThreads = 512;
 constexpr int kApplyThreads = 1024;
+constexpr int kHistBits = 16;              // classify: top key bits histogrammed for buckets
+constexpr int kHistTile = 65535;           // keys per histogram block (16-bit counters)
+constexpr int kHistBins = 1 << kHistBits;
+constexpr int kBucketCap = 8192;           // keys one block sorts in shared memory
+constexpr int kSubBins = 4096;             // counting-sort bins inside one super-bucket
+constexpr int kSubMax = 32;                // largest sub-bin insertion-sorted
+constexpr int kBucketThreads = 1024;
+constexpr int kScatterTile = 16384;        // keys per bucket-scatter block
+constexpr int kMaxSuper = 24576;           // super-buckets the scatter kernel can count
 constexpr int kInsertThreads = 256;
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
@@ -245,6 +255,23 @@ uint64_t sort_scratch_words(uint64_t n, int kw);
 cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint64_t n, int kw,
                        int bits, uint32_t *counts, const uint64_t **result, cudaStream_t s);
 
+// Bucket sort of one-word keys (classify): bucket_histogram counts
+// key >> shift over kHistBins bins; the host merges adjacent bins into
+// super-buckets of at most kBucketCap keys (map: bin -> super-bucket,
+// start: first position of each super-bucket, nsuper + 1 entries);
+// bucket_place_and_sort scatters in -> out by super-bucket and sorts every
+// super-bucket of at most kBucketCap keys in shared memory.  Larger ones (a
+// single bin) are left to the caller.  cursor needs nsuper words.
+uint64_t bucket_hist_blocks(uint64_t n);   // partial histograms: this many x kHistBins u16
+cudaError_t bucket_histogram(const uint64_t *keys, uint64_t n, int shift, unsigned short *partial,
+                             unsigned *hist, cudaStream_t s);
+// lo[b] / rsh[b]: lowest key value of super-bucket b and the shift that
+// maps its key range onto kSubBins sub-bins.
+cudaError_t bucket_place_and_sort(const uint64_t *in, uint64_t *out, uint64_t n, int shift,
+                                  const unsigned *map, unsigned nsuper,
+                                  const unsigned long long *start, const unsigned long long *lo,
+                                  const int *rsh, unsigned long long *cursor, cudaStream_t s);
+
 cudaError_t launch_query(const uint64_t *keys, uint64_t n, int kw, int K, Geometry G,
                          uint32_t *est, cudaStream_t s);
 // est > tau split, stable: trusted keys to out[0, T), erroneous to out[T, n);
@@ -254,6 +281,7 @@ cudaError_t launch_split(const uint64_t *keys, const uint32_t *est, uint64_t n, 
                          uint32_t tau, uint64_t *out, uint64_t *scratch, DevCounters *ctr,
                          cudaStream_t s);
 cudaError_t launch_merge(uint64_t *dst, const uint64_t *src, Geometry G, cudaStream_t s);
+
 cudaError_t launch_count_saturated(Geometry G, DevCounters *ctr, cudaStream_t s);
 
 }  // namespace countbf

@@ -116,37 +116,50 @@ def sample_reads(g: np.ndarray, model: ReadModel, stream: Stream,
     np.cumsum(lens, out=offsets[1:])
     bases = np.empty(int(offsets[-1]), dtype=np.uint8)
     lmax = int(lens.max()) if n else 0
+    # per-base draws come from one raw 64-bit word: bits 32..63 choose the
+    # error type against integer thresholds, bits 0..15 the substitution
+    # (1, 2 or 3 steps round A,C,G,T), bits 16..17 an inserted base
+    t_sub = np.uint64(int(model.sub * 2 ** 32))
+    t_ins = np.uint64(int((model.sub + model.ins) * 2 ** 32))
+    t_del = np.uint64(int((model.sub + model.ins + model.dele) * 2 ** 32))
+    indels = model.ins > 0 or model.dele > 0
+    jj = np.arange(lmax, dtype=np.int64)[None, :]
     for r0 in range(0, n, chunk):
         r1 = min(n, r0 + chunk)
         nr = r1 - r0
         L = lens[r0:r1].astype(np.int64)
         start = stream.integers(nr, G)
-        u = stream.uniform(nr * lmax).reshape(nr, lmax)
-        is_sub = u < model.sub
-        is_ins = (u >= model.sub) & (u < model.sub + model.ins)
-        is_del = (u >= model.sub + model.ins) & (u < model.sub + model.ins + model.dele)
-        adv = np.where(is_ins, 0, np.where(is_del, 2, 1)).astype(np.int64)
-        before = np.cumsum(adv, axis=1) - adv
-        tidx = (start[:, None] + before + is_del.astype(np.int64)) % G
+        raw = stream.raw(nr * lmax).reshape(nr, lmax)
+        top = raw >> np.uint64(32)
+        is_sub = top < t_sub
+        if indels:
+            is_ins = (top >= t_sub) & (top < t_ins)
+            is_del = (top >= t_ins) & (top < t_del)
+            adv = np.where(is_ins, 0, np.where(is_del, 2, 1)).astype(np.int64)
+            before = np.cumsum(adv, axis=1) - adv
+            tidx = (start[:, None] + before + is_del.astype(np.int64)) % G
+        else:
+            tidx = (start[:, None] + jj) % G
         codes = g[tidx]
-        rnd = stream.integers(nr * lmax, 4).reshape(nr, lmax).astype(np.uint8)
-        codes = np.where(is_ins, rnd, codes)
-        shift = (stream.integers(nr * lmax, 3).reshape(nr, lmax) + 1).astype(np.uint8)
-        codes = np.where(is_sub, (codes + shift) % 4, codes).astype(np.uint8)
+        if indels:
+            rnd = ((raw >> np.uint64(16)) & np.uint64(3)).astype(np.uint8)
+            codes = np.where(is_ins, rnd, codes)
+        shift = (((raw & np.uint64(0xFFFF)) * np.uint64(3)) >> np.uint64(16)).astype(np.uint8) + 1
+        codes = np.where(is_sub, (codes + shift) & 3, codes).astype(np.uint8)
         if model.both_strands:
             rev = stream.uniform(nr) < 0.5
         else:
             rev = np.zeros(nr, dtype=bool)
-        is_n = stream.uniform(nr * lmax).reshape(nr, lmax) < model.n_rate
         asc = ASCII[codes]
-        asc[is_n] = ord("N")
+        if model.n_rate > 0:
+            asc[stream.uniform(nr * lmax).reshape(nr, lmax) < model.n_rate] = ord("N")
         # opposite strand: complement (A<->T, C<->G, N stays) and reverse each
         # read within its own length
-        jj = np.arange(lmax, dtype=np.int64)[None, :]
-        src = np.where(rev[:, None], L[:, None] - 1 - jj, jj)
-        src = np.clip(src, 0, lmax - 1)
-        asc = np.take_along_axis(asc, src, axis=1)
-        asc = np.where(rev[:, None], _COMPLEMENT[asc], asc)
+        if rev.any():
+            src = np.where(rev[:, None], L[:, None] - 1 - jj, jj)
+            np.clip(src, 0, lmax - 1, out=src)
+            asc = np.take_along_axis(asc, src, axis=1)
+            asc = np.where(rev[:, None], _COMPLEMENT[asc], asc)
         keep = jj < L[:, None]
         o0, o1 = int(offsets[r0]), int(offsets[r1])
         bases[o0:o1] = asc[keep]

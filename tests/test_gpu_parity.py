@@ -156,6 +156,34 @@ def test_partitioned_overflow_falls_back_exactly():
         check(g, b, o, 21, 8, 4, 3)
 
 
+def test_sort_bucket_larger_than_shared_memory():
+    # 20,000 distinct 31-mers that all begin with AAAAAAA share the top 14 key
+    # bits: one histogram bin holds more keys than a block sorts in shared
+    # memory, so the classification sort takes its radix-sort fallback
+    st = readsim.Stream(77)
+    n = 20000
+    tails = readsim.ASCII[st.integers(n * 24, 4).astype(np.uint8)].reshape(n, 24)
+    heads = np.full((n, 7), ord("A"), np.uint8)
+    b1 = np.concatenate([heads, tails], axis=1).reshape(-1)
+    o1 = np.arange(n + 1, dtype=np.uint64) * np.uint64(31)
+    b2, o2 = readsim.random_reads(2000, 80, 150, seed=78)
+    b = np.concatenate([b1, b2])
+    o = np.concatenate([o1, o2[1:] + o1[-1]])
+    g = gpu_run(b, o, 31, 1 << 22, 4, 4, 2)
+    ref = check(g, b, o, 31, 4, 4, 2)
+    assert int(np.count_nonzero((ref.distinct_lo >> np.uint64(48)) == 0)) > 16384
+
+
+@pytest.mark.parametrize("K", [31, 55])
+def test_nearly_all_windows_distinct(K):
+    # about a million windows of i.i.d. bases are nearly all distinct: the
+    # distinct set grows to the window count and the sort sees ~1e6 keys
+    b, o = readsim.random_reads(8000 if K == 31 else 6000, 150, 150, seed=K)
+    g = gpu_run(b, o, K, 1 << 24, 4, 4, 2)
+    ref = check(g, b, o, K, 4, 4, 2)
+    assert len(ref.distinct_lo) > 0.95 * ref.n_inserted
+
+
 def test_repeated_read_contention():
     # the same read 3000 times: every window hits the same cells and the same
     # distinct-set slot from many threads at once
@@ -199,6 +227,26 @@ def test_batches_accumulate_and_grow_the_distinct_set():
     check(g, b, o, 21, 4, 3, 2)
     g2 = gpu_run(b, o, 21, 1 << 20, 4, 3, 2, batches=batches, device_inputs=False)
     assert np.array_equal(g["counters"], g2["counters"])
+
+
+def test_classify_between_inserts():
+    # classify, insert more reads, classify again: the second result covers
+    # all reads (classify keeps the distinct keys as the key list)
+    b, o = readsim.scaled("tiny", 1200, seed_offset=6).generate()
+    half = 500
+    b1, o1 = b[:int(o[half])].copy(), o[:half + 1].copy()
+    b2, o2 = b[int(o[half]):].copy(), (o[half:] - o[half]).copy()
+    with kc.CountBF(21, 1 << 18, 4, 3, 2) as bf:
+        bf.insert(_dev(b1), _dev(o1))
+        bf.classify()
+        first = bf.stats()["distinct"]
+        bf.insert(_dev(b2), _dev(o2))
+        bf.classify()
+        keys, est = bf.distinct()
+        g = dict(stats=bf.stats(), counters=bf.counters(), keys=keys, est=est,
+                 trusted=bf.trusted(), erroneous=bf.erroneous())
+    ref = check(g, b, o, 21, 4, 3, 2)
+    assert 0 < first < len(ref.distinct_lo)
 
 
 def test_forward_only_strand():
