@@ -289,8 +289,9 @@ def run_ours(args) -> None:
         h_bases = torch.from_numpy(bases).pin_memory()
         h_offsets = torch.from_numpy(offsets.view(np.int64)).pin_memory()
         cap = max(distinct, 1)
-        h_tr = torch.empty(cap, dtype=torch.int64).pin_memory()
-        h_er = torch.empty(cap, dtype=torch.int64).pin_memory()
+        kw = 1 if w.K <= 32 else 2   # 64-bit words per key
+        h_tr = torch.empty(cap * kw, dtype=torch.int64).pin_memory()
+        h_er = torch.empty(cap * kw, dtype=torch.int64).pin_memory()
 
         def e2e_step():
             bf.reset()
@@ -313,7 +314,7 @@ def run_ours(args) -> None:
         assert nt == trusted and nt + ne == distinct
         e2e = {"value": whole_job_rate(inserted, args.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(bases.nbytes + offsets.nbytes),
-               "d2h_bytes_per_step": int(8 * distinct),
+               "d2h_bytes_per_step": int(8 * kw * distinct),
                "note": "reset + insert from pinned host reads + classify + copy of the "
                        "trustworthy and erroneous key lists to pinned host memory; wall clock"}
 
@@ -358,13 +359,181 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- batched
+def _batch_sample(args):
+    """One sample of the batched workload (runs in a worker process)."""
+    i, n_reads, seed = args
+    st = readsim.Stream(seed)
+    g = readsim.genome(1_000_000, 0.5, st)
+    err = 0.005 + 0.015 * float(st.uniform(1)[0])
+    b, o = readsim.sample_reads(g, readsim.ReadModel(n_reads, (50, 300), sub=err), st)
+    return i, b, o, err
+
+
+def batched_workload(n_samples: int, scale: float, seed: int = 4001):
+    """Read counts log-normal (median 1.4e5, sigma 1.2) clipped to [1e4, 2e6],
+    times `scale`; lengths U[50, 300]; 0.5-2% substitutions; a 1 Mb genome
+    per sample."""
+    import multiprocessing as mp
+    st = readsim.Stream(seed)
+    z = np.sqrt(-2 * np.log(st.uniform(n_samples) + 1e-300)) * np.cos(2 * np.pi * st.uniform(n_samples))
+    reads = np.clip(np.exp(np.log(1.4e5) + 1.2 * z), 1e4, 2e6)
+    reads = np.maximum((reads * scale).astype(np.int64), 1)
+    jobs = [(i, int(reads[i]), seed * 1000 + i) for i in range(n_samples)]
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        out = sorted(pool.map(_batch_sample, jobs), key=lambda x: x[0])
+    return out
+
+
+def run_batched(args) -> None:
+    samples = batched_workload(args.samples, args.batch_scale)
+    import torch
+    import paper_2305_07545_gb300 as kc
+    torch.cuda.set_device(0)
+    K, nhash, alpha, tau = 31, 4, 4, 3
+    stream = torch.cuda.Stream()
+    filters, dev, nreads, windows = [], [], [], 0
+    for _, b, o, err in samples:
+        lens = np.diff(o.astype(np.int64))
+        w = int(np.maximum(lens - K + 1, 0).sum())
+        windows += w
+        exp_distinct = 1_000_000 + w * min(1.0, err * K)
+        filters.append(kc.CountBF(K, int(2 * exp_distinct), alpha, nhash, tau,
+                                  stream=stream.cuda_stream, update_mode=kc.UPDATE_ATOMIC))
+        dev.append((torch.from_numpy(b).cuda(), torch.from_numpy(o.view(np.int64)).cuda()))
+        nreads.append(len(o) - 1)
+    torch.cuda.synchronize()
+    batch = kc.Batch(filters)
+    bases = [d[0] for d in dev]
+    offs = [d[1] for d in dev]
+
+    def batched_step():
+        kc.kmerco_batch_insert(batch.b, bases, offs, nreads, reset=True)
+        batch.classify()
+
+    def per_sample_step():
+        for f, (b, o) in zip(filters, dev):
+            f.reset()
+            f.insert(b, o)
+            f.classify()
+
+    def timed(fn, steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def insert_only(fn, steps):
+        return timed(fn, steps)
+
+    for _ in range(args.warmup):
+        batched_step()
+    info = batch.info()
+    t_batched = timed(batched_step, args.steps)
+    ins_batched = insert_only(lambda: kc.kmerco_batch_insert(batch.b, bases, offs, nreads, True),
+                              args.steps)
+    for _ in range(max(1, args.warmup // 2)):
+        per_sample_step()
+    t_single = timed(per_sample_step, args.steps)
+
+    def per_sample_insert():
+        for f, (b, o) in zip(filters, dev):
+            f.reset()
+            f.insert(b, o)
+    ins_single = insert_only(per_sample_insert, args.steps)
+    inserted = sum(f.stats()["inserted"] for f in filters)
+    batch.close()
+    for f in filters:
+        f.close()
+    line = {"metric": METRIC, "value": inserted / (t_batched / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batched,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"batched: {len(samples)} samples, reads log-normal "
+                                   f"(median 1.4e5, sigma 1.2, clipped 1e4..2e6) x {args.batch_scale}, "
+                                   f"50-300 bp, 0.5-2% substitutions, 1 Mb genome each, K=31, "
+                                   f"4-bit counters at 8 bits per expected distinct K-mer, 4 hashes, "
+                                   f"tau=3",
+                       "reads": int(sum(nreads)), "kmers_per_step": int(inserted),
+                       "windows": int(windows), "schedule": info},
+            "per_sample_path": {"value": inserted / (t_single / 1000.0), "ms_per_step": t_single},
+            "insert_only_ms": {"batched": ins_batched, "per_sample": ins_single}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- serving
+def run_serving(args) -> None:
+    samples = batched_workload(args.jobs, args.batch_scale, seed=5001)
+    import torch
+    from paper_2305_07545_gb300 import serve
+    torch.cuda.set_device(0)
+    K, nhash, alpha, tau = 31, 4, 4, 3
+    jobs = []
+    for i, b, o, err in samples:
+        w = serve.window_count(o, K)
+        exp = 1_000_000 + w * min(1.0, err * K)
+        m = 1 << int(np.ceil(np.log2(2 * exp)))      # power-of-two classes share pooled handles
+        jobs.append(serve.Job(torch.from_numpy(b).pin_memory(),
+                              torch.from_numpy(o.view(np.int64)).pin_memory(),
+                              K=K, m=m, counter_bits=alpha, nhash=nhash, tau=tau, name=f"job{i}"))
+    kmers = None
+
+    def run(arrivals):
+        with serve.Server(hbm_budget=args.hbm_budget, slots=args.slots) as srv:
+            for j in jobs[:min(4, len(jobs))]:          # warm the handle pool
+                srv.submit(j).result()
+            t0 = time.perf_counter()
+            res = serve.replay(srv, jobs, arrivals)
+            wall = time.perf_counter() - t0
+            return res, wall, srv.max_running
+
+    res, wall, peak = run([0.0] * len(jobs))
+    kmers = sum(r.inserted for r in res)
+    capacity = len(jobs) / wall
+    rates = []
+    st = readsim.Stream(6001)
+    for factor in (0.25, 0.5, 1.0, 2.0, 4.0):
+        lam = factor * capacity
+        gaps = -np.log(st.uniform(len(jobs)) + 1e-300) / lam
+        arrivals = np.cumsum(gaps) - gaps[0]
+        r, w, pk = run(list(arrivals))
+        lat = np.array([x.latency for x in r]) * 1000.0
+        rates.append({"load": factor, "arrivals_per_s": lam, "kmers_per_s": kmers / w,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "max_concurrent": pk})
+    line = {"metric": METRIC, "value": kmers / wall, "unit": UNIT, "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": wall * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"serving: {len(jobs)} counting jobs drawn from the batched "
+                                   f"workload's sizes (x {args.batch_scale}), K=31, 4 hashes, "
+                                   f"tau=3, Poisson arrivals, HBM budget {args.hbm_budget >> 30} GB, "
+                                   f"{args.slots} slots",
+                       "kmers": int(kmers), "saturated_jobs_per_s": capacity,
+                       "saturated_max_concurrent": peak},
+            "serving": rates}
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="single", choices=sorted(readsim.WORKLOADS))
+    ap.add_argument("--workload", default="single",
+                    choices=sorted(readsim.WORKLOADS) + ["batched", "serving"])
+    ap.add_argument("--jobs", type=int, default=64, help="serving workload: jobs")
+    ap.add_argument("--slots", type=int, default=16, help="serving workload: concurrent jobs")
+    ap.add_argument("--hbm-budget", type=int, default=120 << 30,
+                    help="serving workload: device bytes the jobs may hold")
+    ap.add_argument("--samples", type=int, default=256, help="batched workload: samples")
+    ap.add_argument("--batch-scale", type=float, default=0.25,
+                    help="batched workload: factor on every sample's read count")
     ap.add_argument("--cpu-reads", type=int, default=150_000,
                     help="reads in the bounded CPU-oracle sample")
     ap.add_argument("--ref-reads", type=int, default=25_000,
@@ -378,6 +547,10 @@ def main(argv=None) -> None:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 

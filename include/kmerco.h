@@ -75,6 +75,14 @@ typedef struct {
                               2 partitioned: increments grouped by countBF slice and applied in
                               shared memory (needs k <= 32, nhash <= 4, at most 2^26 cells;
                               otherwise create returns EINVAL) */
+    uint64_t dim_x;        /* two-dimensional countBF (Section 2.1, Algorithm 3): dim_x x dim_y
+                              cells of eta counters; m is then ignored and m_actual is
+                              dim_x * dim_y * eta.  Hash value h selects cell
+                              (h mod dim_x, h mod dim_y), stored row-major at
+                              (h mod dim_x) * dim_y + (h mod dim_y), and counter h mod eta.
+                              Both 0: flat countBF of m counters.  Otherwise both 1..2^24;
+                              the paper takes primes from Eq. 1 (kmerco_paper_dims). */
+    uint64_t dim_y;
 } kmerco_config_t;
 
 /* Running totals and results of one handle (kmerco_stats). */
@@ -90,6 +98,7 @@ typedef struct {
     uint64_t words;              /* 64-bit cells: m_actual / eta */
     uint64_t device_bytes;       /* device memory held by the handle */
     uint64_t launches;           /* CUDA kernels this handle has launched since creation */
+    uint64_t dim_x, dim_y;       /* two-dimensional geometry, or 0, 0 for a flat countBF */
     int k, counter_bits, eta, nhash;
     uint32_t threshold;
     int classified;              /* 1 when trustworthy/erroneous reflect every insert so far */
@@ -110,6 +119,16 @@ typedef struct {
 int kmerco_create(int k, uint64_t m, int counter_bits, int nhash, uint32_t threshold,
                   kmerco_t **out);
 
+/*
+ * countBF dimensions by Eq. 1 (Section 2.1): m = -n ln(FPP) / (ln 2)^2
+ * (the standard Bloom filter size for n items), v = sqrt(m / 128),
+ * dim_x = the smallest prime above v, dim_y = the third prime after dim_x;
+ * the countBF then holds dim_x * dim_y cells of 64 bits.  n is the number of
+ * items the filter is sized for, fpp the false positive probability.
+ * Errors: EINVAL for NULL outputs, n == 0, fpp outside (0, 1), or v >= 2^24.
+ */
+int kmerco_paper_dims(uint64_t n, double fpp, uint64_t *dim_x, uint64_t *dim_y);
+
 /* As kmerco_create() with every option of kmerco_config_t. */
 int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out);
 
@@ -126,7 +145,8 @@ void kmerco_destroy(kmerco_t *h);
  * canonical key (the smaller of the forward and reverse-complement packed
  * values, Section 2.2-2.3) is hashed by H_a = MurmurHash3_x64_128 with seed
  * a, a = 0..k_h-1, first output word; counter g = H_a mod m_actual, cell
- * g / eta, counter g mod eta, is incremented unless it already holds
+ * g / eta, counter g mod eta (a two-dimensional countBF: the cell and
+ * counter of kmerco_config_t.dim_x) is incremented unless it already holds
  * 2^alpha - 1.  The key also joins the handle's distinct-key set.
  * Calls accumulate; order of reads and calls does not change any result.
  * Asynchronous on the handle's stream, except that device-resident offsets
@@ -232,6 +252,52 @@ int kmerco_classify_noalloc(const uint64_t *cells, uint64_t m, int k, int counte
 
 /* Zero the countBF, empty the distinct set and all totals; keeps memory. */
 int kmerco_reset(kmerco_t *h);
+
+/*
+ * Batches: many samples, each with its own handle and countBF, inserted by
+ * one persistent kernel launch (the same per-window work as kmerco_insert,
+ * atomic update design).  The handles must share device, stream, K and the
+ * key width; their m, counter_bits and nhash may differ.  The paper counts
+ * one sample at a time; batching is a GPU schedule, not a change of method.
+ */
+typedef struct kmerco_batch kmerco_batch_t;
+
+typedef struct {
+    int samples;
+    int chunk;            /* window starts per work unit chosen by the autotuner */
+    int blocks_per_sm;    /* resident blocks per SM chosen by the autotuner */
+    int tuned;            /* 1 after the first reset-insert tuned the schedule */
+    float tuned_ms;       /* device time of the best schedule when it was tuned */
+    int graph;            /* 1 when a CUDA graph of reset + insert is captured */
+    uint64_t launches;    /* kernels launched by the batch */
+    uint64_t total_chunks;
+} kmerco_batch_info_t;
+
+/* Group n handles (not owned; they must outlive the batch).  EINVAL when
+ * they differ in device, stream, K or key width, or repeat. */
+int kmerco_batch_create(kmerco_t *const *handles, int n, kmerco_batch_t **out);
+
+/* Release the batch (not its handles).  NULL is ignored. */
+void kmerco_batch_destroy(kmerco_batch_t *b);
+
+/*
+ * Insert sample i's reads (device pointers bases[i], offsets[i], nreads[i],
+ * the CSR layout of kmerco_insert) into handle i, all in one launch.  With
+ * reset != 0 every handle is first reset (kmerco_reset).  The first reset
+ * call times every candidate schedule (chunk 1024/2048 x resident blocks)
+ * on this input, keeps the fastest, and captures reset + insert in a CUDA
+ * graph; a later call with the same pointers and read counts replays it.
+ * Asynchronous except for the planning of a new input (one readback).
+ * Errors: EINVAL (host pointers, decreasing offsets, mixed K); ENOMEM; ECUDA.
+ */
+int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
+                        const uint64_t *const *offsets, const uint64_t *nreads, int reset);
+
+/* kmerco_classify() of every handle of the batch, in order. */
+int kmerco_batch_classify(kmerco_batch_t *b);
+
+/* Schedule and counters of the batch. */
+int kmerco_batch_info(kmerco_batch_t *b, kmerco_batch_info_t *info);
 
 /* Static description of a status code; never NULL. */
 const char *kmerco_strerror(int status);

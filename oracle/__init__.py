@@ -41,7 +41,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C, -O2, no target-specific flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC],
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"],
                        check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -93,6 +93,19 @@ def lib() -> ctypes.CDLL:
                                       ctypes.c_uint64, _u64p, _u8p]
         L.oracle_classify.restype = ctypes.c_uint64
         L.oracle_merge.argtypes = [_u64p, _u64p, ctypes.c_uint64, ctypes.c_int]
+        L.oracle_insert_sequential_2d.argtypes = [_u64p, _u64p, ctypes.c_uint64, ctypes.c_int,
+                                                  ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                                  ctypes.c_int, _u64p]
+        L.oracle_insert_sequential_2d.restype = None
+        L.oracle_query_2d.argtypes = [_u64p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_int]
+        L.oracle_query_2d.restype = ctypes.c_uint64
+        L.oracle_classify_2d.argtypes = [_u64p, _u64p, _u64p, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_uint64, _u64p, _u8p]
+        L.oracle_classify_2d.restype = ctypes.c_uint64
+        L.oracle_paper_dims.argtypes = [ctypes.c_uint64, ctypes.c_double, _u64p, _u64p]
+        L.oracle_paper_dims.restype = ctypes.c_int
         L.oracle_merge.restype = None
         _lib = L
     return _lib
@@ -244,6 +257,47 @@ def classify(filt: np.ndarray, dhi: np.ndarray, dlo: np.ndarray, K: int, m: int,
     return est[:d].copy(), tr[:d].astype(bool)
 
 
+def paper_dims(n: int, fpp: float = 0.001) -> tuple[int, int]:
+    """Eq. 1: the prime dimensions (X, Y) of a countBF sized for n items."""
+    x = ctypes.c_uint64(0)
+    y = ctypes.c_uint64(0)
+    if lib().oracle_paper_dims(n, fpp, ctypes.byref(x), ctypes.byref(y)) != 0:
+        raise ValueError("paper_dims: n must be >= 1 and 0 < fpp < 1")
+    return int(x.value), int(y.value)
+
+
+def insert_sequential_2d(hi: np.ndarray, lo: np.ndarray, K: int, dims: tuple[int, int],
+                         alpha: int, nhash: int, filt: np.ndarray | None = None) -> np.ndarray:
+    """Algorithm 3 on a two-dimensional countBF of X x Y cells (row-major)."""
+    X, Y = dims
+    _check_params(K, X * Y * eta(alpha), alpha, nhash)
+    hi = np.ascontiguousarray(hi, np.uint64)
+    lo = np.ascontiguousarray(lo, np.uint64)
+    if filt is None:
+        filt = np.zeros(X * Y, np.uint64)
+    lib().oracle_insert_sequential_2d(_p(hi, _u64p), _p(lo, _u64p), len(lo), K, X, Y, alpha,
+                                      nhash, _p(filt, _u64p))
+    return filt
+
+
+def query_2d(filt: np.ndarray, K: int, hi: int, lo: int, dims: tuple[int, int], alpha: int,
+             nhash: int) -> int:
+    return int(lib().oracle_query_2d(_p(filt, _u64p), K, hi, lo, dims[0], dims[1], alpha, nhash))
+
+
+def classify_2d(filt: np.ndarray, dhi: np.ndarray, dlo: np.ndarray, K: int,
+                dims: tuple[int, int], alpha: int, nhash: int, tau: int):
+    dhi = np.ascontiguousarray(dhi, np.uint64)
+    dlo = np.ascontiguousarray(dlo, np.uint64)
+    d = len(dlo)
+    est = np.zeros(max(d, 1), np.uint64)
+    tr = np.zeros(max(d, 1), np.uint8)
+    if d:
+        lib().oracle_classify_2d(_p(filt, _u64p), _p(dhi, _u64p), _p(dlo, _u64p), d, K, dims[0],
+                                 dims[1], alpha, nhash, tau, _p(est, _u64p), _p(tr, _u8p))
+    return est[:d].copy(), tr[:d].astype(bool)
+
+
 def merge(dst: np.ndarray, src: np.ndarray, m: int, alpha: int) -> np.ndarray:
     """Counter-wise saturating sum of two filters, in place in ``dst``."""
     lib().oracle_merge(_p(dst, _u64p), _p(np.ascontiguousarray(src, np.uint64), _u64p), m, alpha)
@@ -265,12 +319,21 @@ class Result:
 
 def run(bases: np.ndarray, offsets: np.ndarray, K: int, m: int, alpha: int, nhash: int,
         tau: int, canonical: bool = True, cross_check: bool = True,
-        with_counts: bool = False) -> Result:
+        with_counts: bool = False, dims: tuple[int, int] | None = None) -> Result:
     """The whole path: extract -> countBF -> distinct -> classify.
 
     With ``cross_check`` the filter is built both by the closed form and by
-    the sequential Algorithm 3 loop, and the two must be identical.
+    the sequential Algorithm 3 loop, and the two must be identical.  With
+    ``dims = (X, Y)`` the countBF is two-dimensional (m is ignored; the
+    closed form exists for the flat layout only, so there is no cross-check).
     """
+    if dims is not None:
+        ex = extract(bases, offsets, K, canonical)
+        filt = insert_sequential_2d(ex.hi, ex.lo, K, dims, alpha, nhash)
+        dhi, dlo, cnt = distinct(ex.hi, ex.lo)
+        est, tr = classify_2d(filt, dhi, dlo, K, dims, alpha, nhash, tau)
+        return Result(filt, dhi, dlo, est, tr, ex.n_windows, ex.n_skipped, ex.n,
+                      cnt if with_counts else None)
     _check_params(K, m, alpha, nhash)
     ex = extract(bases, offsets, K, canonical)
     filt = insert_sequential(ex.hi, ex.lo, K, m, alpha, nhash)

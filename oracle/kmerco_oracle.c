@@ -48,6 +48,7 @@
  *   query / split    no-underestimate against exact counts, exact estimates
  *                    where no collision occurs, the tau boundary.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -254,25 +255,48 @@ static uint64_t read_counter(const uint64_t *filter, uint64_t w, int alpha, int 
 }
 
 /*
+ * Cell w and counter l that hash value h selects.
+ *   Two-dimensional countBF of x * y cells (x > 0; Algorithm 3 as printed):
+ *     i = h mod x, j = h mod y, l = h mod eta; the cell C[i][j] of the
+ *     x-by-y array sits at w = i * y + j (row-major).
+ *   Flat countBF of m counters (x == 0): g = h mod m, w = g / eta,
+ *     l = g mod eta.  For x, y, eta pairwise coprime and m = x * y * eta the
+ *     two are the same map up to relabelling (Chinese remainder theorem).
+ */
+static void address(uint64_t h, uint64_t m, uint64_t x, uint64_t y, int alpha,
+                    uint64_t *w, int *l)
+{
+    uint64_t eta = (uint64_t)oracle_eta(alpha);
+    if (x) {
+        uint64_t i = h % x, j = h % y;
+        *w = i * y + j;
+        *l = (int)(h % eta);
+    } else {
+        uint64_t g = h % m;
+        *w = g / eta;
+        *l = (int)(g % eta);
+    }
+}
+
+/*
  * Sequential IcountBF (Algorithm 3) applied to every key in input order.
- * For each hash a: g = H_a(x) mod m, cell g / eta, counter g mod eta;
+ * For each hash a: the cell and counter of H_a(x) (address() above);
  * extract, add one, and write back with the reset mask -- unless the
  * counter already holds 2^alpha - 1, in which case it is left alone and the
  * loop continues with the next a (per-counter reading of the overflow
  * branch).  The filter is updated in place.
  */
-void oracle_insert_sequential(const uint64_t *hi, const uint64_t *lo, uint64_t n,
-                              int K, uint64_t m, int alpha, int nhash,
-                              uint64_t *filter)
+static void insert_sequential(const uint64_t *hi, const uint64_t *lo, uint64_t n,
+                              int K, uint64_t m, uint64_t dx, uint64_t dy, int alpha,
+                              int nhash, uint64_t *filter)
 {
-    uint64_t eta = (uint64_t)oracle_eta(alpha);
     uint64_t maxc = (1ULL << alpha) - 1;
     for (uint64_t x = 0; x < n; ++x) {
         for (int a = 0; a < nhash; ++a) {
             uint64_t h = oracle_kmer_hash(K, hi[x], lo[x], (uint32_t)a);
-            uint64_t g = h % m;
-            uint64_t w = g / eta;
-            int l = (int)(g % eta);
+            uint64_t w;
+            int l;
+            address(h, m, dx, dy, alpha, &w, &l);
             uint64_t value = read_counter(filter, w, alpha, l);
             if (value == maxc) continue; /* would overflow: stays saturated */
             value += 1;
@@ -280,6 +304,22 @@ void oracle_insert_sequential(const uint64_t *hi, const uint64_t *lo, uint64_t n
             filter[w] = (filter[w] & oracle_reset_mask(alpha, l)) | value;
         }
     }
+}
+
+/* Flat countBF of m counters. */
+void oracle_insert_sequential(const uint64_t *hi, const uint64_t *lo, uint64_t n,
+                              int K, uint64_t m, int alpha, int nhash,
+                              uint64_t *filter)
+{
+    insert_sequential(hi, lo, n, K, m, 0, 0, alpha, nhash, filter);
+}
+
+/* Two-dimensional countBF of dx * dy cells. */
+void oracle_insert_sequential_2d(const uint64_t *hi, const uint64_t *lo, uint64_t n,
+                                 int K, uint64_t dx, uint64_t dy, int alpha, int nhash,
+                                 uint64_t *filter)
+{
+    insert_sequential(hi, lo, n, K, 0, dx, dy, alpha, nhash, filter);
 }
 
 /*
@@ -309,18 +349,31 @@ void oracle_counters_closed_form(const uint64_t *hi, const uint64_t *lo, uint64_
  * QcountBF-II (Algorithm 5): for each a read counter H_a(x) mod m; return
  * 0 as soon as one is zero, otherwise the minimum over a.
  */
-uint64_t oracle_query(const uint64_t *filter, int K, uint64_t hi, uint64_t lo,
-                      uint64_t m, int alpha, int nhash)
+static uint64_t query(const uint64_t *filter, int K, uint64_t hi, uint64_t lo, uint64_t m,
+                      uint64_t dx, uint64_t dy, int alpha, int nhash)
 {
-    uint64_t eta = (uint64_t)oracle_eta(alpha);
     uint64_t best = ~0ULL;
     for (int a = 0; a < nhash; ++a) {
-        uint64_t g = oracle_kmer_hash(K, hi, lo, (uint32_t)a) % m;
-        uint64_t value = read_counter(filter, g / eta, alpha, (int)(g % eta));
+        uint64_t w;
+        int l;
+        address(oracle_kmer_hash(K, hi, lo, (uint32_t)a), m, dx, dy, alpha, &w, &l);
+        uint64_t value = read_counter(filter, w, alpha, l);
         if (value == 0) return 0;
         if (value < best) best = value;
     }
     return best;
+}
+
+uint64_t oracle_query(const uint64_t *filter, int K, uint64_t hi, uint64_t lo,
+                      uint64_t m, int alpha, int nhash)
+{
+    return query(filter, K, hi, lo, m, 0, 0, alpha, nhash);
+}
+
+uint64_t oracle_query_2d(const uint64_t *filter, int K, uint64_t hi, uint64_t lo,
+                         uint64_t dx, uint64_t dy, int alpha, int nhash)
+{
+    return query(filter, K, hi, lo, 0, dx, dy, alpha, nhash);
 }
 
 /*
@@ -389,17 +442,31 @@ uint64_t oracle_distinct(const uint64_t *hi, const uint64_t *lo, uint64_t n,
  * = QcountBF-II of key i; trusted[i] = 1 when est[i] > tau (frequency
  * "more than" tau), else 0 (erroneous).  Returns the number trusted.
  */
-uint64_t oracle_classify(const uint64_t *filter, const uint64_t *dhi, const uint64_t *dlo,
-                         uint64_t d, int K, uint64_t m, int alpha, int nhash,
-                         uint64_t tau, uint64_t *est, uint8_t *trusted)
+static uint64_t classify(const uint64_t *filter, const uint64_t *dhi, const uint64_t *dlo,
+                         uint64_t d, int K, uint64_t m, uint64_t dx, uint64_t dy, int alpha,
+                         int nhash, uint64_t tau, uint64_t *est, uint8_t *trusted)
 {
     uint64_t t = 0;
     for (uint64_t i = 0; i < d; ++i) {
-        est[i] = oracle_query(filter, K, dhi[i], dlo[i], m, alpha, nhash);
+        est[i] = query(filter, K, dhi[i], dlo[i], m, dx, dy, alpha, nhash);
         trusted[i] = est[i] > tau;
         t += trusted[i];
     }
     return t;
+}
+
+uint64_t oracle_classify(const uint64_t *filter, const uint64_t *dhi, const uint64_t *dlo,
+                         uint64_t d, int K, uint64_t m, int alpha, int nhash,
+                         uint64_t tau, uint64_t *est, uint8_t *trusted)
+{
+    return classify(filter, dhi, dlo, d, K, m, 0, 0, alpha, nhash, tau, est, trusted);
+}
+
+uint64_t oracle_classify_2d(const uint64_t *filter, const uint64_t *dhi, const uint64_t *dlo,
+                            uint64_t d, int K, uint64_t dx, uint64_t dy, int alpha, int nhash,
+                            uint64_t tau, uint64_t *est, uint8_t *trusted)
+{
+    return classify(filter, dhi, dlo, d, K, 0, dx, dy, alpha, nhash, tau, est, trusted);
 }
 
 /*
@@ -419,4 +486,41 @@ void oracle_merge(uint64_t *dst, const uint64_t *src, uint64_t m, int alpha)
         if (s > maxc) s = maxc;
         dst[w] = (dst[w] & oracle_reset_mask(alpha, l)) | (s << (alpha * l));
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* countBF sizing (Section 2.1, Eq. 1)                                       */
+/* ------------------------------------------------------------------------ */
+
+static int is_prime(uint64_t p)
+{
+    if (p < 2) return 0;
+    for (uint64_t d = 2; d * d <= p; ++d)
+        if (p % d == 0) return 0;
+    return 1;
+}
+
+/*
+ * Eq. 1: the standard Bloom filter size for n items at false positive
+ * probability fpp is m = -n ln(fpp) / (ln 2)^2 bits; v = sqrt(m / 128);
+ * X is the smallest prime greater than v and Y the third prime after X
+ * (counting X's successors in the sequence of primes).  The countBF then
+ * holds X * Y cells of beta = 64 bits.  Returns 0, or -1 for bad input.
+ */
+int oracle_paper_dims(uint64_t n, double fpp, uint64_t *X, uint64_t *Y)
+{
+    if (n == 0 || !(fpp > 0.0 && fpp < 1.0)) return -1;
+    double m = -(double)n * log(fpp) / (log(2.0) * log(2.0));
+    double v = sqrt(m / 128.0);
+    uint64_t x = (uint64_t)v;
+    while ((double)x <= v || !is_prime(x)) ++x;
+    uint64_t y = x;
+    int primes_after = 0;
+    while (primes_after < 3) {
+        ++y;
+        if (is_prime(y)) ++primes_after;
+    }
+    *X = x;
+    *Y = y;
+    return 0;
 }

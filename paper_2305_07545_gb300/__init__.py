@@ -27,16 +27,27 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ESIZE = range(7)
 class kmerco_config_t(ctypes.Structure):
     _fields_ = [("k", c_int), ("m", c_uint64), ("counter_bits", c_int), ("nhash", c_int),
                 ("threshold", c_uint32), ("forward_only", c_int), ("stream", c_void_p),
-                ("hbm_budget", c_uint64), ("device", c_int), ("update_mode", c_int)]
+                ("hbm_budget", c_uint64), ("device", c_int), ("update_mode", c_int),
+                ("dim_x", c_uint64), ("dim_y", c_uint64)]
 
 
 class kmerco_stats_t(ctypes.Structure):
     _fields_ = [("windows", c_uint64), ("n_skipped", c_uint64), ("inserted", c_uint64),
                 ("distinct", c_uint64), ("trustworthy", c_uint64), ("erroneous", c_uint64),
                 ("saturated_counters", c_uint64), ("m_actual", c_uint64), ("words", c_uint64),
-                ("device_bytes", c_uint64), ("launches", c_uint64), ("k", c_int), ("counter_bits", c_int),
+                ("device_bytes", c_uint64), ("launches", c_uint64), ("dim_x", c_uint64),
+                ("dim_y", c_uint64), ("k", c_int), ("counter_bits", c_int),
                 ("eta", c_int), ("nhash", c_int), ("threshold", c_uint32),
                 ("classified", c_int), ("insert_ms", c_float), ("classify_ms", c_float)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class kmerco_batch_info_t(ctypes.Structure):
+    _fields_ = [("samples", c_int), ("chunk", c_int), ("blocks_per_sm", c_int), ("tuned", c_int),
+                ("tuned_ms", c_float), ("graph", c_int), ("launches", c_uint64),
+                ("total_chunks", c_uint64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -56,6 +67,7 @@ _u32p = POINTER(c_uint32)
 SIGNATURES = {
     "kmerco_create": (c_int, [c_int, c_uint64, c_int, c_int, c_uint32, POINTER(c_void_p)]),
     "kmerco_create_ex": (c_int, [POINTER(kmerco_config_t), POINTER(c_void_p)]),
+    "kmerco_paper_dims": (c_int, [c_uint64, ctypes.c_double, _u64p, _u64p]),
     "kmerco_destroy": (None, [c_void_p]),
     "kmerco_insert": (c_int, [c_void_p, c_void_p, c_void_p, c_uint64]),
     "kmerco_classify": (c_int, [c_void_p]),
@@ -70,6 +82,11 @@ SIGNATURES = {
     "kmerco_strerror": (c_char_p, [c_int]),
     "kmerco_classify_noalloc": (c_int, [c_void_p, c_uint64, c_int, c_int, c_int, c_uint32,
                                         c_void_p, c_uint64, c_void_p, c_void_p, _u64p, c_void_p]),
+    "kmerco_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
+    "kmerco_batch_destroy": (None, [c_void_p]),
+    "kmerco_batch_insert": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), _u64p, c_int]),
+    "kmerco_batch_classify": (c_int, [c_void_p]),
+    "kmerco_batch_info": (c_int, [c_void_p, c_void_p]),
 }
 
 NOALLOC_MAX_KEYS = 1 << 28
@@ -135,12 +152,21 @@ UPDATE_AUTO, UPDATE_ATOMIC, UPDATE_PARTITIONED = 0, 1, 2
 
 def kmerco_create_ex(k: int, m: int, counter_bits: int, nhash: int, threshold: int,
                      forward_only: bool = False, stream: int | None = None,
-                     hbm_budget: int = 0, device: int = -1, update_mode: int = 0) -> int:
+                     hbm_budget: int = 0, device: int = -1, update_mode: int = 0,
+                     dims: tuple[int, int] | None = None) -> int:
+    dx, dy = dims if dims is not None else (0, 0)
     cfg = kmerco_config_t(k, m, counter_bits, nhash, threshold, int(forward_only),
-                          stream or None, hbm_budget, device, update_mode)
+                          stream or None, hbm_budget, device, update_mode, dx, dy)
     h = c_void_p()
     _check(load().kmerco_create_ex(byref(cfg), byref(h)), "kmerco_create_ex")
     return h.value
+
+
+def kmerco_paper_dims(n: int, fpp: float = 0.001) -> tuple[int, int]:
+    """Eq. 1 countBF dimensions (X, Y) for n items at false positive probability fpp."""
+    x, y = c_uint64(0), c_uint64(0)
+    _check(load().kmerco_paper_dims(n, fpp, byref(x), byref(y)), "kmerco_paper_dims")
+    return x.value, y.value
 
 
 def kmerco_destroy(h: int) -> None:
@@ -210,6 +236,36 @@ def kmerco_classify_noalloc(cells, m: int, k: int, counter_bits: int, nhash: int
     return nt.value
 
 
+def kmerco_batch_create(handles: list[int]) -> int:
+    arr = (c_void_p * len(handles))(*handles)
+    b = c_void_p()
+    _check(load().kmerco_batch_create(arr, len(handles), byref(b)), "kmerco_batch_create")
+    return b.value
+
+
+def kmerco_batch_destroy(b: int) -> None:
+    load().kmerco_batch_destroy(b)
+
+
+def kmerco_batch_insert(b: int, bases: list, offsets: list, nreads: list[int],
+                        reset: bool = True) -> None:
+    n = len(nreads)
+    pb = (c_void_p * n)(*[_ptr(x) for x in bases])
+    po = (c_void_p * n)(*[_ptr(x) for x in offsets])
+    pn = (c_uint64 * n)(*nreads)
+    _check(load().kmerco_batch_insert(b, pb, po, pn, int(reset)), "kmerco_batch_insert")
+
+
+def kmerco_batch_classify(b: int) -> None:
+    _check(load().kmerco_batch_classify(b), "kmerco_batch_classify")
+
+
+def kmerco_batch_info(b: int) -> dict:
+    info = kmerco_batch_info_t()
+    _check(load().kmerco_batch_info(b, byref(info)), "kmerco_batch_info")
+    return info.as_dict()
+
+
 # ------------------------------------------------------------------ wrapper
 class CountBF:
     """One countBF handle with numpy results.
@@ -220,11 +276,14 @@ class CountBF:
 
     def __init__(self, k: int, m: int, counter_bits: int = 4, nhash: int = 4,
                  threshold: int = 3, forward_only: bool = False, stream: int | None = None,
-                 hbm_budget: int = 0, device: int = -1, update_mode: int = UPDATE_AUTO):
+                 hbm_budget: int = 0, device: int = -1, update_mode: int = UPDATE_AUTO,
+                 dims: tuple[int, int] | None = None):
+        """``dims = (X, Y)`` makes a two-dimensional countBF of X x Y cells
+        (Algorithm 3's addressing; ``m`` is then ignored)."""
         self.k = k
         self.kw = 1 if k <= 32 else 2
         self.h = kmerco_create_ex(k, m, counter_bits, nhash, threshold, forward_only, stream,
-                                  hbm_budget, device, update_mode)
+                                  hbm_budget, device, update_mode, dims)
 
     def close(self) -> None:
         if self.h:
@@ -292,3 +351,31 @@ class CountBF:
 
     def merge(self, other: "CountBF") -> None:
         kmerco_merge(self.h, other.h)
+
+
+class Batch:
+    """Several CountBF handles inserted by one persistent launch."""
+
+    def __init__(self, filters: list[CountBF]):
+        self.filters = list(filters)
+        self.b = kmerco_batch_create([f.h for f in self.filters])
+
+    def close(self) -> None:
+        if self.b:
+            kmerco_batch_destroy(self.b)
+            self.b = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def insert(self, bases: list, offsets: list, reset: bool = True) -> None:
+        kmerco_batch_insert(self.b, bases, offsets, [len(o) - 1 for o in offsets], reset)
+
+    def classify(self) -> None:
+        kmerco_batch_classify(self.b)
+
+    def info(self) -> dict:
+        return kmerco_batch_info(self.b)

@@ -1,10 +1,12 @@
 // Host side of the countBF C ABI (include/kmerco.h): argument validation,
 // device memory, pointer-kind detection, capacity management of the
 // distinct-key set, and the order of kernel launches for each phase.
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -198,14 +200,20 @@ int validate(const kmerco_config_t *c) {
     if (c->k < 1 || c->k > 64) return KMERCO_EINVAL;
     if (c->counter_bits < 1 || c->counter_bits > 32) return KMERCO_EINVAL;
     if (c->nhash < 1 || c->nhash > 32) return KMERCO_EINVAL;
-    if (c->m < 1 || c->m > (1ull << 48)) return KMERCO_EINVAL;
+    if (c->dim_x || c->dim_y) {
+        // two-dimensional countBF: m is implied by the dimensions
+        if (c->dim_x < 1 || c->dim_y < 1 || c->dim_x > (1ull << 24) || c->dim_y > (1ull << 24))
+            return KMERCO_EINVAL;
+    } else if (c->m < 1 || c->m > (1ull << 48)) {
+        return KMERCO_EINVAL;
+    }
     const uint64_t maxc = (1ull << c->counter_bits) - 1;
     if ((uint64_t)c->threshold >= maxc) return KMERCO_EINVAL;
     if (c->forward_only != 0 && c->forward_only != 1) return KMERCO_EINVAL;
     if (c->update_mode < 0 || c->update_mode > 2) return KMERCO_EINVAL;
     if (c->update_mode == 2) {
         const uint64_t eta = 64 / (uint64_t)c->counter_bits;
-        const uint64_t words = (c->m + eta - 1) / eta;
+        const uint64_t words = c->dim_x ? c->dim_x * c->dim_y : (c->m + eta - 1) / eta;
         if (c->k > 32 || c->nhash > kPartMaxHash || words > (1ull << (kMaxCoarseShift + 6)))
             return KMERCO_EINVAL;
     }
@@ -219,6 +227,14 @@ bool use_partitioned(const kmerco_t *h) {
                       h->G.words <= (1ull << (kMaxCoarseShift + 6));
     if (h->update_mode == 2) return able;
     return able && h->G.words >= (1ull << 17);   // smaller countBFs stay L2-resident
+}
+
+// Trial division; n is at most about 2^24 here.
+bool is_prime(uint64_t n) {
+    if (n < 2) return false;
+    for (uint64_t d = 2; d * d <= n; ++d)
+        if (n % d == 0) return false;
+    return true;
 }
 
 // Smallest l with 2^l >= x (64 for x above 2^63).
@@ -243,6 +259,22 @@ const char *kmerco_strerror(int status) {
     case KMERCO_ESIZE: return "buffer too small";
     default: return "unknown status";
     }
+}
+
+int kmerco_paper_dims(uint64_t n, double fpp, uint64_t *dim_x, uint64_t *dim_y) {
+    if (!dim_x || !dim_y || n < 1 || !(fpp > 0.0 && fpp < 1.0)) return KMERCO_EINVAL;
+    const double ln2 = log(2.0);
+    const double m = -(double)n * log(fpp) / (ln2 * ln2);   // standard Bloom filter size
+    const double v = sqrt(m / 128.0);
+    if (!(v < (double)(1ull << 24))) return KMERCO_EINVAL;
+    uint64_t x = (uint64_t)floor(v) + 1;                     // first integer above v
+    while (!is_prime(x)) ++x;
+    uint64_t y = x;
+    for (int found = 0; found < 3;)                          // third prime after x
+        if (is_prime(++y)) ++found;
+    *dim_x = x;
+    *dim_y = y;
+    return KMERCO_OK;
 }
 
 int kmerco_create(int k, uint64_t m, int counter_bits, int nhash, uint32_t threshold,
@@ -303,17 +335,9 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
         h->grid_part = sms * insert_blocks_per_sm(1, true);
 
         const uint64_t eta = (uint64_t)h->eta;
+        h->G = make_geometry((cfg->m + eta - 1) / eta, cfg->dim_x, cfg->dim_y, h->alpha,
+                             h->nhash);
         Geometry &G = h->G;
-        G.alpha = h->alpha;
-        G.eta = h->eta;
-        G.nhash = h->nhash;
-        G.words = (cfg->m + eta - 1) / eta;
-        G.m = G.words * eta;
-        G.m_mask = (G.m & (G.m - 1)) == 0 ? G.m - 1 : 0;
-        G.maxc = (1ull << h->alpha) - 1;
-        G.eta_log2 = -1;
-        for (int b = 0; b < 7; ++b)
-            if ((1 << b) == h->eta) G.eta_log2 = b;
         void *p;
         if ((status = dev_alloc(h, &p, G.words * 8))) break;
         G.cells = (uint64_t *)p;
@@ -672,6 +696,8 @@ int kmerco_stats(kmerco_t *h, kmerco_stats_t *s) {
     s->saturated_counters = c.saturated;
     s->m_actual = h->G.m;
     s->words = h->G.words;
+    s->dim_x = h->G.dim_x;
+    s->dim_y = h->G.dim_y;
     s->device_bytes = h->used;
     s->launches = h->launches;
     s->k = h->K;
@@ -775,7 +801,8 @@ int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est) {
 
 int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
     if (!dst || !src || dst == src) return KMERCO_EINVAL;
-    if (dst->K != src->K || dst->G.m != src->G.m || dst->alpha != src->alpha ||
+    if (dst->K != src->K || dst->G.m != src->G.m || dst->G.dim_x != src->G.dim_x ||
+        dst->G.dim_y != src->G.dim_y || dst->alpha != src->alpha ||
         dst->nhash != src->nhash || dst->canonical != src->canonical || dst->device != src->device)
         return KMERCO_EINVAL;
     DeviceGuard guard(dst->device);
@@ -797,6 +824,302 @@ int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
                             cudaMemcpyHostToDevice, dst->stream));
     KM_CUDA(cudaStreamSynchronize(dst->stream));
     dst->classified = false;
+    return KMERCO_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches
+struct kmerco_batch {
+    std::vector<kmerco_t *> h;
+    int n, kw, device;
+    cudaStream_t stream;
+    int sms;
+    InsertArgs *d_args;                      // per sample
+    unsigned long long *d_chunk_end;         // inclusive prefix of chunks
+    unsigned long long *d_bound;             // kBoundOutWords per sample
+    const uint64_t **d_offs;                 // device copies of the pointer arrays
+    uint64_t *d_nreads;
+    std::vector<InsertArgs> args;
+    std::vector<unsigned long long> chunk_end, bound_host;
+    std::vector<const char *> p_bases;       // inputs of the planned launch
+    std::vector<const uint64_t *> p_offs;
+    std::vector<uint64_t> p_nreads;
+    bool planned, tuned, have_graph;
+    int chunk, bpm;
+    float tuned_ms;
+    unsigned long long total_chunks;
+    uint64_t launches;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaEvent_t ev[2];
+};
+
+namespace {
+
+// Build the per-sample arguments for chunk size `chunk` and upload them.
+int batch_build_args(kmerco_batch *b, int chunk) {
+    b->args.resize(b->n);
+    b->chunk_end.resize(b->n);
+    unsigned long long acc = 0;
+    for (int i = 0; i < b->n; ++i) {
+        kmerco_t *h = b->h[i];
+        const unsigned long long *bo = &b->bound_host[(size_t)i * kBoundOutWords];
+        const uint64_t first = bo[1], last = bo[2];
+        const uint64_t nchunks = bo[0] ? (last - first + chunk - 1) / chunk : 0;
+        InsertArgs &a = b->args[i];
+        memset(&a, 0, sizeof(a));
+        a.bases = (const uint8_t *)b->p_bases[i] + first;
+        a.offsets = b->p_offs[i];
+        a.nreads = b->p_nreads[i];
+        a.first = first;
+        a.last = last;
+        a.first_read = h->first_read;
+        a.nchunks = nchunks;
+        a.K = h->K;
+        a.canonical = h->canonical;
+        a.G = h->G;
+        a.table = h->table;
+        a.cap = h->cap;
+        a.dlist = h->dlist;
+        a.dlist_cap = h->dlist_cap;
+        a.ctr = h->ctr;
+        acc += nchunks;
+        b->chunk_end[i] = acc;
+    }
+    b->total_chunks = acc;
+    KM_CUDA(cudaMemcpyAsync(b->d_args, b->args.data(), b->n * sizeof(InsertArgs),
+                            cudaMemcpyHostToDevice, b->stream));
+    KM_CUDA(cudaMemcpyAsync(b->d_chunk_end, b->chunk_end.data(), b->n * sizeof(unsigned long long),
+                            cudaMemcpyHostToDevice, b->stream));
+    KM_CUDA(cudaStreamSynchronize(b->stream));
+    return KMERCO_OK;
+}
+
+// Reset every sample on the stream (capturable: memsets only).
+int batch_reset_device(kmerco_batch *b) {
+    for (kmerco_t *h : b->h) {
+        KM_CUDA(cudaMemsetAsync(h->G.cells, 0, h->G.words * 8, b->stream));
+        if (h->table) KM_CUDA(cudaMemsetAsync(h->table, 0xFF, h->cap * h->kw * 8, b->stream));
+        KM_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), b->stream));
+    }
+    return KMERCO_OK;
+}
+
+int batch_launch(kmerco_batch *b, int chunk, int bpm) {
+    KM_CUDA(launch_insert_batch(b->d_args, b->d_chunk_end, b->n, b->total_chunks, b->kw, chunk,
+                                b->sms * bpm, b->stream));
+    b->launches += b->total_chunks ? 2 : 0;
+    return KMERCO_OK;
+}
+
+void batch_mark_inserted(kmerco_batch *b) {
+    for (kmerco_t *h : b->h) {
+        h->classified = false;
+        h->n_distinct = h->n_trusted = 0;
+        h->insert_timed = h->classify_timed = false;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int kmerco_batch_create(kmerco_t *const *handles, int n, kmerco_batch_t **out) {
+    if (!out) return KMERCO_EINVAL;
+    *out = nullptr;
+    if (!handles || n < 1 || n > 65535) return KMERCO_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        if (!handles[i]) return KMERCO_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (handles[j] == handles[i]) return KMERCO_EINVAL;
+        if (handles[i]->device != handles[0]->device || handles[i]->stream != handles[0]->stream ||
+            handles[i]->K != handles[0]->K)
+            return KMERCO_EINVAL;
+    }
+    kmerco_batch *b = new (std::nothrow) kmerco_batch();
+    if (!b) return KMERCO_ENOMEM;
+    b->h.assign(handles, handles + n);
+    b->n = n;
+    b->kw = handles[0]->kw;
+    b->device = handles[0]->device;
+    b->stream = handles[0]->stream;
+    b->chunk = kChunk;
+    b->bpm = 4;
+    DeviceGuard guard(b->device);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (b->sms <= 0) b->sms = 1;
+    const int mx = insert_batch_blocks_per_sm(b->kw, kChunk);
+    if (b->bpm > mx) b->bpm = mx;
+    bool ok = cudaMalloc((void **)&b->d_args, n * sizeof(InsertArgs)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_chunk_end, n * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_bound, (size_t)n * kBoundOutWords * 8) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_offs, n * sizeof(uint64_t *)) == cudaSuccess &&
+              cudaMalloc((void **)&b->d_nreads, n * sizeof(uint64_t)) == cudaSuccess &&
+              cudaEventCreate(&b->ev[0]) == cudaSuccess && cudaEventCreate(&b->ev[1]) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        kmerco_batch_destroy(b);
+        return KMERCO_ENOMEM;
+    }
+    *out = b;
+    return KMERCO_OK;
+}
+
+void kmerco_batch_destroy(kmerco_batch_t *b) {
+    if (!b) return;
+    {
+        DeviceGuard guard(b->device);
+        if (b->stream) cudaStreamSynchronize(b->stream);
+        if (b->have_graph) {
+            cudaGraphExecDestroy(b->exec);
+            cudaGraphDestroy(b->graph);
+        }
+        cudaFree(b->d_args);
+        cudaFree(b->d_chunk_end);
+        cudaFree(b->d_bound);
+        cudaFree(b->d_offs);
+        cudaFree(b->d_nreads);
+        for (int i = 0; i < 2; ++i)
+            if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+        cudaGetLastError();
+    }
+    delete b;
+}
+
+int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
+                        const uint64_t *const *offsets, const uint64_t *nreads, int reset) {
+    if (!b || !bases || !offsets || !nreads) return KMERCO_EINVAL;
+    DeviceGuard guard(b->device);
+    // the same inputs as the captured launch: replay the graph
+    bool same = b->planned && reset && b->have_graph;
+    for (int i = 0; same && i < b->n; ++i)
+        same = b->p_bases[i] == bases[i] && b->p_offs[i] == offsets[i] && b->p_nreads[i] == nreads[i];
+    if (same) {
+        KM_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        b->launches += b->total_chunks ? 2 : 0;
+        batch_mark_inserted(b);
+        return KMERCO_OK;
+    }
+    uint64_t max_reads = 0;
+    for (int i = 0; i < b->n; ++i) {
+        if (nreads[i] >= 0xFFFFFFFFull) return KMERCO_EINVAL;
+        if (nreads[i] && (!offsets[i] || !is_device_ptr(offsets[i]))) return KMERCO_EINVAL;
+        if (bases[i] && !is_device_ptr(bases[i])) return KMERCO_EINVAL;
+        if (nreads[i] > max_reads) max_reads = nreads[i];
+    }
+    b->p_bases.assign(bases, bases + b->n);
+    b->p_offs.assign(offsets, offsets + b->n);
+    b->p_nreads.assign(nreads, nreads + b->n);
+    if (b->have_graph) {
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->have_graph = false;
+    }
+    // plan: window bounds and offsets of every sample in one launch
+    KM_CUDA(cudaMemcpyAsync(b->d_offs, b->p_offs.data(), b->n * sizeof(uint64_t *),
+                            cudaMemcpyHostToDevice, b->stream));
+    KM_CUDA(cudaMemcpyAsync(b->d_nreads, nreads, b->n * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                            b->stream));
+    KM_CUDA(launch_window_bound_batch(b->d_offs, b->d_nreads, b->n, b->h[0]->K, b->d_bound,
+                                      max_reads, b->stream));
+    b->launches += 1;
+    b->bound_host.resize((size_t)b->n * kBoundOutWords);
+    KM_CUDA(cudaMemcpyAsync(b->bound_host.data(), b->d_bound, (size_t)b->n * kBoundOutWords * 8,
+                            cudaMemcpyDeviceToHost, b->stream));
+    KM_CUDA(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        if (b->bound_host[(size_t)i * kBoundOutWords + 3]) return KMERCO_EINVAL;
+        if (b->bound_host[(size_t)i * kBoundOutWords + 2] > b->bound_host[(size_t)i * kBoundOutWords + 1] &&
+            !bases[i])
+            return KMERCO_EINVAL;
+    }
+    // capacities (host work; never inside a capture)
+    for (int i = 0; i < b->n; ++i) {
+        kmerco_t *h = b->h[i];
+        if (reset) KM_TRY(kmerco_reset(h));
+        const unsigned long long *bo = &b->bound_host[(size_t)i * kBoundOutWords];
+        KM_TRY(ensure_set_capacity(h, bo[0]));
+        const uint64_t most = (bo[2] - bo[1] + 1023) / 1024;   // chunks at the smallest chunk size
+        KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, most ? most : 1));
+    }
+    KM_CUDA(cudaStreamSynchronize(b->stream));
+    b->planned = true;
+    // autotune once per batch: chunk size x resident blocks, timed on this input
+    if (reset && !b->tuned) {
+        const int chunks[2] = {1024, 2048};
+        float best = 1e30f;
+        for (int c : chunks) {
+            KM_TRY(batch_build_args(b, c));
+            const int mx = insert_batch_blocks_per_sm(b->kw, c);
+            for (int bpm = 2; bpm <= mx && bpm <= 8; ++bpm) {
+                KM_TRY(batch_reset_device(b));
+                KM_CUDA(cudaEventRecord(b->ev[0], b->stream));
+                KM_TRY(batch_launch(b, c, bpm));
+                KM_CUDA(cudaEventRecord(b->ev[1], b->stream));
+                KM_CUDA(cudaEventSynchronize(b->ev[1]));
+                float ms = 0;
+                cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+                if (ms < best) {
+                    best = ms;
+                    b->chunk = c;
+                    b->bpm = bpm;
+                }
+            }
+        }
+        b->tuned = true;
+        b->tuned_ms = best;
+    }
+    KM_TRY(batch_build_args(b, b->chunk));
+    if (reset) {
+        // reset + insert of every sample as one CUDA graph (plain launches on
+        // a stream that cannot be captured, such as the legacy default stream)
+        if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            KM_TRY(batch_reset_device(b));
+            KM_TRY(batch_launch(b, b->chunk, b->bpm));
+        } else {
+            int st = batch_reset_device(b);
+            if (st == KMERCO_OK) st = batch_launch(b, b->chunk, b->bpm);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+            if (st != KMERCO_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            KM_CUDA(ec);
+            if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return KMERCO_ECUDA;
+            }
+            b->graph = g;
+            b->have_graph = true;
+            KM_CUDA(cudaGraphLaunch(b->exec, b->stream));
+        }
+    } else {
+        KM_TRY(batch_launch(b, b->chunk, b->bpm));
+    }
+    batch_mark_inserted(b);
+    return KMERCO_OK;
+}
+
+int kmerco_batch_classify(kmerco_batch_t *b) {
+    if (!b) return KMERCO_EINVAL;
+    for (kmerco_t *h : b->h) KM_TRY(kmerco_classify(h));
+    return KMERCO_OK;
+}
+
+int kmerco_batch_info(kmerco_batch_t *b, kmerco_batch_info_t *info) {
+    if (!b || !info) return KMERCO_EINVAL;
+    memset(info, 0, sizeof(*info));
+    info->samples = b->n;
+    info->chunk = b->chunk;
+    info->blocks_per_sm = b->bpm;
+    info->tuned = b->tuned ? 1 : 0;
+    info->tuned_ms = b->tuned_ms;
+    info->graph = b->have_graph ? 1 : 0;
+    info->launches = b->launches;
+    info->total_chunks = b->total_chunks;
     return KMERCO_OK;
 }
 

@@ -233,9 +233,9 @@ __global__ void query_kernel(const uint64_t *keys, uint64_t n, int K, Geometry G
             else
                 murmur16(klo, khi, (uint32_t)a, h1, h2);
             uint64_t cell;
-            unsigned sh;
-            locate(G, counter_of(G, h1), cell, sh);
-            const uint64_t v = (__ldg(G.cells + cell) >> sh) & G.maxc;
+            unsigned slot;
+            address(G, h1, cell, slot);
+            const uint64_t v = (__ldg(G.cells + cell) >> (slot * (unsigned)G.alpha)) & G.maxc;
             if (v == 0) {
                 best = 0;
                 break;

@@ -162,304 +162,339 @@ __device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64
     }
 }
 
-// Cell and counter index of counter g (cell g / eta, counter g mod eta).
-__device__ __forceinline__ void locate_slot(const Geometry &G, uint64_t g, uint64_t &cell,
-                                            unsigned &slot) {
-    if (G.eta_log2 >= 0) {
-        cell = g >> G.eta_log2;
-        slot = (unsigned)(g & (uint64_t)(G.eta - 1));
-    } else {
-        cell = g / (uint64_t)G.eta;
-        slot = (unsigned)(g - cell * (uint64_t)G.eta);
+// One chunk of CHUNK window starts (steps 1-5 above) for the sample
+// described by `a`; counts its windows into my_windows / my_skipped.
+template <int KW, int CHUNK, bool PART>
+__device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chunk,
+                                              InsertSmem<KW, CHUNK, PART> &S, uint64_t pol_keep,
+                                              uint64_t pol_stream,
+                                              unsigned long long &my_windows,
+                                              unsigned long long &my_skipped) {
+    constexpr int kPack32 = ChunkDims<CHUNK>::kPack32;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = a.K;
+    const uint64_t total = a.last - a.first;
+    const Geometry &G = a.G;
+    const uint64_t c0 = chunk * (uint64_t)CHUNK;
+    const uint64_t e = min(c0 + (uint64_t)(CHUNK + K - 1), total);
+    const unsigned nb = (unsigned)(e - c0);
+    const uintptr_t src = (uintptr_t)(a.bases + c0);
+    const unsigned head = (unsigned)(src & 15);
+    const uintptr_t abase = src - head;
+
+    // 1. stage bytes [c0, e) at raw[head ...]: whole 16-byte vectors
+    //    inside the range with streaming loads, partial ones bytewise.
+    const unsigned nvec = (head + nb + 15) >> 4;
+    for (unsigned v = tid; v < nvec; v += kInsertThreads) {
+        unsigned lo = v << 4, hi = lo + 16;
+        if (lo >= head && hi <= head + nb) {
+            *(uint4 *)(S.raw + lo) = __ldcs((const uint4 *)(abase + lo));
+        } else {
+            for (unsigned b = lo; b < hi; ++b)
+                if (b >= head && b < head + nb) S.raw[b] = *(const uint8_t *)(abase + b);
+        }
     }
+    for (int i = tid; i < kPack32 / 2; i += kInsertThreads) S.brk[i] = 0;
+    if (tid == 0) {
+        S.nvalid = 0;
+        S.nfresh = 0;
+        S.nupd = 0;
+    }
+    if (PART && tid < kCoarseBins) {
+        S.hist[tid] = 0;
+        S.fill[tid] = 0;
+    }
+    __syncthreads();
+
+    // 2a. pack: 16 bases per thread -> 2-bit codes + invalid bits
+    for (int t = tid; t < kPack32; t += kInsertThreads) {
+        uint32_t code = 0, bad = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            unsigned q = (unsigned)t * 16 + j;
+            unsigned c = q < nb ? S.raw[head + q] : 'N';
+            unsigned u = c | 0x20u;
+            bool ok = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
+            unsigned cd = ((c >> 1) ^ (c >> 2)) & 3u;   // A,a->0 C,c->1 G,g->2 T,t->3
+            code = (code << 2) | (ok ? cd : 0u);
+            bad |= (ok ? 0u : 1u) << j;
+        }
+        S.pk[t ^ 1] = code;
+        S.inv[t] = (uint16_t)bad;
+    }
+    // 2b. read starts inside the staged span
+    for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; r < a.nreads; r += kInsertThreads) {
+        uint64_t s = a.offsets[r] - a.first;
+        if (s >= c0 + nb) break;
+        if (s < c0) continue;   // only with decreasing offsets, which the host rejects
+        unsigned q = (unsigned)(s - c0);
+        if (q > 0) atomicOr(&S.brk[q >> 5], 1u << (q & 31));
+    }
+    __syncthreads();
+
+    // 3. window starts: inside one read, K valid bases
+    const uint64_t *inv64 = (const uint64_t *)S.inv;
+    const uint64_t *brk64 = (const uint64_t *)S.brk;
+    const uint64_t maskK = K == 64 ? ~0ull : ((1ull << K) - 1);
+    const uint64_t maskK1 = (1ull << (K - 1)) - 1;
+    for (int p0 = 0; p0 < CHUNK; p0 += kInsertThreads) {
+        unsigned p = (unsigned)(p0 + tid);
+        bool window = p + (unsigned)K <= nb && (bits_at(brk64, p + 1) & maskK1) == 0;
+        bool valid = window && (bits_at(inv64, p) & maskK) == 0;
+        my_windows += window;
+        my_skipped += window && !valid;
+        unsigned bal = __ballot_sync(0xffffffffu, valid);
+        unsigned base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&S.nvalid, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (valid) S.vpos[base + __popc(bal & ((1u << lane) - 1))] = (uint16_t)p;
+    }
+    __syncthreads();
+
+    // 4. per valid window: canonical key, hashes, counter updates, set insert
+    const unsigned nvalid = S.nvalid;
+    const uint64_t *pk64 = (const uint64_t *)S.pk;
+    for (unsigned i0 = (unsigned)warp * 32; i0 < nvalid; i0 += kInsertThreads) {
+        const unsigned i = i0 + lane;
+        const bool active = i < nvalid;
+        uint64_t klo = 0, khi = 0;
+        if (active) {
+            const unsigned p = S.vpos[i];
+            const unsigned w = p >> 5, s = (p & 31) * 2;
+            const uint64_t x0 = pk64[w], x1 = pk64[w + 1];
+            const uint64_t t0 = s ? (x0 << s) | (x1 >> (64 - s)) : x0;
+            if (KW == 1) {
+                const uint64_t fwd = t0 >> (64 - 2 * K);
+                klo = fwd;
+                if (a.canonical) {
+                    const uint64_t rc = revcomp64(fwd, K);
+                    klo = rc < fwd ? rc : fwd;
+                }
+            } else {
+                const uint64_t x2 = pk64[w + 2];
+                const uint64_t t1 = s ? (x1 << s) | (x2 >> (64 - s)) : x1;
+                const int r = 128 - 2 * K;   // 0..62
+                uint64_t fhi, flo;
+                if (r == 0) {
+                    fhi = t0;
+                    flo = t1;
+                } else {
+                    flo = (t1 >> r) | (t0 << (64 - r));
+                    fhi = t0 >> r;
+                }
+                klo = flo;
+                khi = fhi;
+                if (a.canonical) {
+                    uint64_t rhi, rlo;
+                    revcomp128(fhi, flo, K, rhi, rlo);
+                    if (rhi < fhi || (rhi == fhi && rlo < flo)) {
+                        klo = rlo;
+                        khi = rhi;
+                    }
+                }
+            }
+        }
+
+        // All loads of a group of four hashes (and, in the first group,
+        // the distinct-set home slot) are issued together, then all
+        // first compare-and-swap attempts; only failed attempts retry.
+        uint64_t table_hash = 0, table_first = kEmptyKey - 1;
+        const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
+        for (int a0 = 0; a0 < G.nhash; a0 += 4) {
+            uint64_t cell[4], cur[4], prev[4];
+            unsigned sh[4], slot[4];
+            bool use[4], need[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                use[j] = active && (a0 + j < G.nhash);
+                cell[j] = 0;
+                sh[j] = 0;
+                slot[j] = 0;
+                if (use[j]) {
+                    uint64_t h1, h2;
+                    if (KW == 1)
+                        murmur8(k1m, (uint32_t)(a0 + j), h1, h2);
+                    else
+                        murmur16(klo, khi, (uint32_t)(a0 + j), h1, h2);
+                    if (a0 + j == 0) table_hash = h2;
+                    address(G, h1, cell[j], slot[j]);
+                    sh[j] = slot[j] * (unsigned)G.alpha;
+                }
+            }
+            if (KW == 1 && a0 == 0 && active)
+                table_first = load_hint(a.table + __umul64hi(table_hash, a.cap), pol_stream);
+            if (PART) {
+                // stage one 32-bit code per increment: coarse region (6 bits),
+                // cell within the region (20 bits), counter within the cell
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, use[j]);
+                    unsigned base = 0;
+                    if (lane == 0 && bal) base = atomicAdd(&S.nupd, (unsigned)__popc(bal));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (use[j]) {
+                        const unsigned bin = (unsigned)(cell[j] >> a.coarse_shift);
+                        const uint32_t code = (bin << 26) |
+                            ((uint32_t)(cell[j] & ((1ull << a.coarse_shift) - 1)) << 6) | slot[j];
+                        S.staged[base + __popc(bal & ((1u << lane) - 1))] = code;
+                        atomicAdd(&S.hist[bin], 1u);
+                    }
+                }
+                continue;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (use[j]) cur[j] = load_hint(G.cells + cell[j], pol_keep);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                need[j] = use[j] && ((cur[j] >> sh[j]) & G.maxc) != G.maxc;
+                prev[j] = cur[j];
+                if (need[j])
+                    prev[j] = atomicCAS((unsigned long long *)(G.cells + cell[j]),
+                                        (unsigned long long)cur[j],
+                                        (unsigned long long)(cur[j] + (1ull << sh[j])));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (need[j] && prev[j] != cur[j])
+                    sat_increment(G.cells, cell[j], sh[j], G.maxc, prev[j], &a.ctr->error);
+        }
+
+        bool isnew = false;
+        if (active)
+            isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, &a.ctr->error,
+                                   pol_stream, table_first);
+        const unsigned bal = __ballot_sync(0xffffffffu, isnew);
+        unsigned base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&S.nfresh, (unsigned)__popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (isnew) {
+            const unsigned slot = base + __popc(bal & ((1u << lane) - 1));
+            S.fresh[slot * KW] = klo;
+            if (KW == 2) S.fresh[slot * KW + 1] = khi;
+        }
+    }
+    __syncthreads();
+
+    if (PART) {
+        // 4b. counting sort of the increment codes by coarse region, one
+        //     cursor atomic per region, coalesced runs into the regions
+        const unsigned nupd = S.nupd;
+        if (tid < kCoarseBins) {
+            unsigned pre = 0;
+            for (int b = 0; b < tid; ++b) pre += S.hist[b];
+            S.start[tid] = pre;
+            const unsigned n = S.hist[tid];
+            unsigned long long b0 = ~0ull;
+            if (n) {
+                b0 = atomicAdd(a.coarse_cursor + tid, (unsigned long long)n);
+                if (b0 + n > a.coarse_cap)
+                    b0 = ~0ull;   // region full: these go to the global fallback
+                else
+                    atomicAdd(a.coarse_written + tid, (unsigned long long)n);
+            }
+            S.base[tid] = b0;
+        }
+        __syncthreads();
+        for (unsigned i = tid; i < nupd; i += kInsertThreads) {
+            const uint32_t code = S.staged[i];
+            const unsigned bin = code >> 26;
+            S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = code;
+        }
+        __syncthreads();
+        for (unsigned i = tid; i < nupd; i += kInsertThreads) {
+            const uint32_t code = S.sorted[i];
+            const unsigned bin = code >> 26;
+            const unsigned long long b0 = S.base[bin];
+            if (b0 != ~0ull) {
+                a.coarse[(uint64_t)bin * a.coarse_cap + b0 + (i - S.start[bin])] = code;
+            } else {
+                const uint64_t cell = ((uint64_t)bin << a.coarse_shift) |
+                                      ((code >> 6) & ((1u << a.coarse_shift) - 1));
+                const unsigned shift = (code & 63u) * (unsigned)G.alpha;
+                sat_increment(G.cells, cell, shift, G.maxc, load_cg(G.cells + cell),
+                              &a.ctr->error);
+            }
+        }
+        __syncthreads();
+    }
+
+    // 5. append this chunk's new keys to the distinct list
+    const unsigned nfresh = S.nfresh;
+    if (nfresh) {
+        if (tid == 0) {
+            unsigned long long b = atomicAdd(&a.ctr->distinct, (unsigned long long)nfresh);
+            if (b + nfresh > a.dlist_cap) {
+                atomicOr(&a.ctr->error, kErrListFull);
+                b = ~0ull;
+            }
+            S.fresh_base = b;
+        }
+        __syncthreads();
+        const unsigned long long b = S.fresh_base;
+        if (b != ~0ull)
+            for (unsigned i = tid; i < nfresh * KW; i += kInsertThreads)
+                a.dlist[b * KW + i] = S.fresh[i];
+    }
+    __syncthreads();
+}
+
+// Warp totals of windows and skipped windows into a sample's counters.
+__device__ __forceinline__ void flush_totals(DevCounters *ctr, unsigned long long &w,
+                                             unsigned long long &k) {
+    for (int o = 16; o; o >>= 1) {
+        w += __shfl_down_sync(0xffffffffu, w, o);
+        k += __shfl_down_sync(0xffffffffu, k, o);
+    }
+    if ((threadIdx.x & 31) == 0 && w) {
+        atomicAdd(&ctr->windows, w);
+        atomicAdd(&ctr->skipped, k);
+        atomicAdd(&ctr->inserted, w - k);
+    }
+    w = 0;
+    k = 0;
 }
 
 template <int KW, int CHUNK, bool PART>
 __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a) {
     __shared__ InsertSmem<KW, CHUNK, PART> S;
-    constexpr int kPack32 = ChunkDims<CHUNK>::kPack32;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = a.K;
-    const uint64_t total = a.last - a.first;
-    const Geometry G = a.G;
     const uint64_t pol_keep = policy_keep(), pol_stream = policy_stream();
     unsigned long long my_windows = 0, my_skipped = 0;
+    for (uint64_t chunk = blockIdx.x; chunk < a.nchunks; chunk += gridDim.x)
+        process_chunk<KW, CHUNK, PART>(a, chunk, S, pol_keep, pol_stream, my_windows, my_skipped);
+    flush_totals(a.ctr, my_windows, my_skipped);
+}
 
-    for (uint64_t chunk = blockIdx.x; chunk < a.nchunks; chunk += gridDim.x) {
-        const uint64_t c0 = chunk * (uint64_t)CHUNK;
-        const uint64_t e = min(c0 + (uint64_t)(CHUNK + K - 1), total);
-        const unsigned nb = (unsigned)(e - c0);
-        const uintptr_t src = (uintptr_t)(a.bases + c0);
-        const unsigned head = (unsigned)(src & 15);
-        const uintptr_t abase = src - head;
-
-        // 1. stage bytes [c0, e) at raw[head ...]: whole 16-byte vectors
-        //    inside the range with streaming loads, partial ones bytewise.
-        const unsigned nvec = (head + nb + 15) >> 4;
-        for (unsigned v = tid; v < nvec; v += kInsertThreads) {
-            unsigned lo = v << 4, hi = lo + 16;
-            if (lo >= head && hi <= head + nb) {
-                *(uint4 *)(S.raw + lo) = __ldcs((const uint4 *)(abase + lo));
-            } else {
-                for (unsigned b = lo; b < hi; ++b)
-                    if (b >= head && b < head + nb) S.raw[b] = *(const uint8_t *)(abase + b);
-            }
-        }
-        for (int i = tid; i < kPack32 / 2; i += kInsertThreads) S.brk[i] = 0;
-        if (tid == 0) {
-            S.nvalid = 0;
-            S.nfresh = 0;
-            S.nupd = 0;
-        }
-        if (PART && tid < kCoarseBins) {
-            S.hist[tid] = 0;
-            S.fill[tid] = 0;
-        }
-        __syncthreads();
-
-        // 2a. pack: 16 bases per thread -> 2-bit codes + invalid bits
-        for (int t = tid; t < kPack32; t += kInsertThreads) {
-            uint32_t code = 0, bad = 0;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                unsigned q = (unsigned)t * 16 + j;
-                unsigned c = q < nb ? S.raw[head + q] : 'N';
-                unsigned u = c | 0x20u;
-                bool ok = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
-                unsigned cd = ((c >> 1) ^ (c >> 2)) & 3u;   // A,a->0 C,c->1 G,g->2 T,t->3
-                code = (code << 2) | (ok ? cd : 0u);
-                bad |= (ok ? 0u : 1u) << j;
-            }
-            S.pk[t ^ 1] = code;
-            S.inv[t] = (uint16_t)bad;
-        }
-        // 2b. read starts inside the staged span
-        for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; r < a.nreads; r += kInsertThreads) {
-            uint64_t s = a.offsets[r] - a.first;
-            if (s >= c0 + nb) break;
-            if (s < c0) continue;   // only with decreasing offsets, which the host rejects
-            unsigned q = (unsigned)(s - c0);
-            if (q > 0) atomicOr(&S.brk[q >> 5], 1u << (q & 31));
-        }
-        __syncthreads();
-
-        // 3. window starts: inside one read, K valid bases
-        const uint64_t *inv64 = (const uint64_t *)S.inv;
-        const uint64_t *brk64 = (const uint64_t *)S.brk;
-        const uint64_t maskK = K == 64 ? ~0ull : ((1ull << K) - 1);
-        const uint64_t maskK1 = (1ull << (K - 1)) - 1;
-        for (int p0 = 0; p0 < CHUNK; p0 += kInsertThreads) {
-            unsigned p = (unsigned)(p0 + tid);
-            bool window = p + (unsigned)K <= nb && (bits_at(brk64, p + 1) & maskK1) == 0;
-            bool valid = window && (bits_at(inv64, p) & maskK) == 0;
-            my_windows += window;
-            my_skipped += window && !valid;
-            unsigned bal = __ballot_sync(0xffffffffu, valid);
-            unsigned base = 0;
-            if (lane == 0 && bal) base = atomicAdd(&S.nvalid, (unsigned)__popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (valid) S.vpos[base + __popc(bal & ((1u << lane) - 1))] = (uint16_t)p;
-        }
-        __syncthreads();
-
-        // 4. per valid window: canonical key, hashes, counter updates, set insert
-        const unsigned nvalid = S.nvalid;
-        const uint64_t *pk64 = (const uint64_t *)S.pk;
-        for (unsigned i0 = (unsigned)warp * 32; i0 < nvalid; i0 += kInsertThreads) {
-            const unsigned i = i0 + lane;
-            const bool active = i < nvalid;
-            uint64_t klo = 0, khi = 0;
-            if (active) {
-                const unsigned p = S.vpos[i];
-                const unsigned w = p >> 5, s = (p & 31) * 2;
-                const uint64_t x0 = pk64[w], x1 = pk64[w + 1];
-                const uint64_t t0 = s ? (x0 << s) | (x1 >> (64 - s)) : x0;
-                if (KW == 1) {
-                    const uint64_t fwd = t0 >> (64 - 2 * K);
-                    klo = fwd;
-                    if (a.canonical) {
-                        const uint64_t rc = revcomp64(fwd, K);
-                        klo = rc < fwd ? rc : fwd;
-                    }
-                } else {
-                    const uint64_t x2 = pk64[w + 2];
-                    const uint64_t t1 = s ? (x1 << s) | (x2 >> (64 - s)) : x1;
-                    const int r = 128 - 2 * K;   // 0..62
-                    uint64_t fhi, flo;
-                    if (r == 0) {
-                        fhi = t0;
-                        flo = t1;
-                    } else {
-                        flo = (t1 >> r) | (t0 << (64 - r));
-                        fhi = t0 >> r;
-                    }
-                    klo = flo;
-                    khi = fhi;
-                    if (a.canonical) {
-                        uint64_t rhi, rlo;
-                        revcomp128(fhi, flo, K, rhi, rlo);
-                        if (rhi < fhi || (rhi == fhi && rlo < flo)) {
-                            klo = rlo;
-                            khi = rhi;
-                        }
-                    }
-                }
-            }
-
-            // All loads of a group of four hashes (and, in the first group,
-            // the distinct-set home slot) are issued together, then all
-            // first compare-and-swap attempts; only failed attempts retry.
-            uint64_t table_hash = 0, table_first = kEmptyKey - 1;
-            const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
-            for (int a0 = 0; a0 < G.nhash; a0 += 4) {
-                uint64_t cell[4], cur[4], prev[4];
-                unsigned sh[4], slot[4];
-                bool use[4], need[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    use[j] = active && (a0 + j < G.nhash);
-                    cell[j] = 0;
-                    sh[j] = 0;
-                    slot[j] = 0;
-                    if (use[j]) {
-                        uint64_t h1, h2;
-                        if (KW == 1)
-                            murmur8(k1m, (uint32_t)(a0 + j), h1, h2);
-                        else
-                            murmur16(klo, khi, (uint32_t)(a0 + j), h1, h2);
-                        if (a0 + j == 0) table_hash = h2;
-                        locate_slot(G, counter_of(G, h1), cell[j], slot[j]);
-                        sh[j] = slot[j] * (unsigned)G.alpha;
-                    }
-                }
-                if (KW == 1 && a0 == 0 && active)
-                    table_first = load_hint(a.table + __umul64hi(table_hash, a.cap), pol_stream);
-                if (PART) {
-                    // stage one 32-bit code per increment: coarse region (6 bits),
-                    // cell within the region (20 bits), counter within the cell
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const unsigned bal = __ballot_sync(0xffffffffu, use[j]);
-                        unsigned base = 0;
-                        if (lane == 0 && bal) base = atomicAdd(&S.nupd, (unsigned)__popc(bal));
-                        base = __shfl_sync(0xffffffffu, base, 0);
-                        if (use[j]) {
-                            const unsigned bin = (unsigned)(cell[j] >> a.coarse_shift);
-                            const uint32_t code = (bin << 26) |
-                                ((uint32_t)(cell[j] & ((1ull << a.coarse_shift) - 1)) << 6) | slot[j];
-                            S.staged[base + __popc(bal & ((1u << lane) - 1))] = code;
-                            atomicAdd(&S.hist[bin], 1u);
-                        }
-                    }
-                    continue;
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (use[j]) cur[j] = load_hint(G.cells + cell[j], pol_keep);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    need[j] = use[j] && ((cur[j] >> sh[j]) & G.maxc) != G.maxc;
-                    prev[j] = cur[j];
-                    if (need[j])
-                        prev[j] = atomicCAS((unsigned long long *)(G.cells + cell[j]),
-                                            (unsigned long long)cur[j],
-                                            (unsigned long long)(cur[j] + (1ull << sh[j])));
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (need[j] && prev[j] != cur[j])
-                        sat_increment(G.cells, cell[j], sh[j], G.maxc, prev[j], &a.ctr->error);
-            }
-
-            bool isnew = false;
-            if (active)
-                isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, &a.ctr->error,
-                                       pol_stream, table_first);
-            const unsigned bal = __ballot_sync(0xffffffffu, isnew);
-            unsigned base = 0;
-            if (lane == 0 && bal) base = atomicAdd(&S.nfresh, (unsigned)__popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (isnew) {
-                const unsigned slot = base + __popc(bal & ((1u << lane) - 1));
-                S.fresh[slot * KW] = klo;
-                if (KW == 2) S.fresh[slot * KW + 1] = khi;
-            }
-        }
-        __syncthreads();
-
-        if (PART) {
-            // 4b. counting sort of the increment codes by coarse region, one
-            //     cursor atomic per region, coalesced runs into the regions
-            const unsigned nupd = S.nupd;
-            if (tid < kCoarseBins) {
-                unsigned pre = 0;
-                for (int b = 0; b < tid; ++b) pre += S.hist[b];
-                S.start[tid] = pre;
-                const unsigned n = S.hist[tid];
-                unsigned long long b0 = ~0ull;
-                if (n) {
-                    b0 = atomicAdd(a.coarse_cursor + tid, (unsigned long long)n);
-                    if (b0 + n > a.coarse_cap)
-                        b0 = ~0ull;   // region full: these go to the global fallback
-                    else
-                        atomicAdd(a.coarse_written + tid, (unsigned long long)n);
-                }
-                S.base[tid] = b0;
-            }
+// Many samples in one persistent launch (atomic update design): the chunks
+// of all samples form one index space, sample s owning chunks
+// [chunk_end[s-1], chunk_end[s]).  A block walks its chunks in increasing
+// order, so the sample only moves forward; its arguments are kept in
+// shared memory and its totals are flushed when it changes.
+template <int KW, int CHUNK>
+__global__ void __launch_bounds__(kInsertThreads, 4) insert_batch_kernel(
+    const InsertArgs *args, const unsigned long long *chunk_end, int nsamples,
+    unsigned long long total_chunks) {
+    __shared__ InsertSmem<KW, CHUNK, false> S;
+    __shared__ InsertArgs A;
+    const uint64_t pol_keep = policy_keep(), pol_stream = policy_stream();
+    unsigned long long my_windows = 0, my_skipped = 0;
+    int s = -1;
+    unsigned long long s_begin = 0;
+    for (unsigned long long chunk = blockIdx.x; chunk < total_chunks; chunk += gridDim.x) {
+        int t = s < 0 ? 0 : s;
+        while (t < nsamples && chunk >= chunk_end[t]) ++t;   // uniform across the block
+        if (t != s) {
+            if (s >= 0) flush_totals(A.ctr, my_windows, my_skipped);
             __syncthreads();
-            for (unsigned i = tid; i < nupd; i += kInsertThreads) {
-                const uint32_t code = S.staged[i];
-                const unsigned bin = code >> 26;
-                S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = code;
-            }
-            __syncthreads();
-            for (unsigned i = tid; i < nupd; i += kInsertThreads) {
-                const uint32_t code = S.sorted[i];
-                const unsigned bin = code >> 26;
-                const unsigned long long b0 = S.base[bin];
-                if (b0 != ~0ull) {
-                    a.coarse[(uint64_t)bin * a.coarse_cap + b0 + (i - S.start[bin])] = code;
-                } else {
-                    const uint64_t cell = ((uint64_t)bin << a.coarse_shift) |
-                                          ((code >> 6) & ((1u << a.coarse_shift) - 1));
-                    const unsigned shift = (code & 63u) * (unsigned)G.alpha;
-                    sat_increment(G.cells, cell, shift, G.maxc, load_cg(G.cells + cell),
-                                  &a.ctr->error);
-                }
-            }
+            if (threadIdx.x == 0) A = args[t];
+            s = t;
+            s_begin = t ? chunk_end[t - 1] : 0;
             __syncthreads();
         }
-
-        // 5. append this chunk's new keys to the distinct list
-        const unsigned nfresh = S.nfresh;
-        if (nfresh) {
-            if (tid == 0) {
-                unsigned long long b = atomicAdd(&a.ctr->distinct, (unsigned long long)nfresh);
-                if (b + nfresh > a.dlist_cap) {
-                    atomicOr(&a.ctr->error, kErrListFull);
-                    b = ~0ull;
-                }
-                S.fresh_base = b;
-            }
-            __syncthreads();
-            const unsigned long long b = S.fresh_base;
-            if (b != ~0ull)
-                for (unsigned i = tid; i < nfresh * KW; i += kInsertThreads)
-                    a.dlist[b * KW + i] = S.fresh[i];
-        }
-        __syncthreads();
+        process_chunk<KW, CHUNK, false>(A, chunk - s_begin, S, pol_keep, pol_stream, my_windows,
+                                        my_skipped);
     }
-
-    // totals: one atomic per warp
-    for (int o = 16; o; o >>= 1) {
-        my_windows += __shfl_down_sync(0xffffffffu, my_windows, o);
-        my_skipped += __shfl_down_sync(0xffffffffu, my_skipped, o);
-    }
-    if (lane == 0 && my_windows) {
-        atomicAdd(&a.ctr->windows, my_windows);
-        atomicAdd(&a.ctr->skipped, my_skipped);
-        atomicAdd(&a.ctr->inserted, my_windows - my_skipped);
-    }
+    if (s >= 0) flush_totals(A.ctr, my_windows, my_skipped);
 }
 
 // Sum over reads of max(0, len - K + 1); flags decreasing offsets.
@@ -500,6 +535,66 @@ __global__ void first_read_kernel(const uint64_t *offsets, uint64_t nreads, uint
             lo = mid + 1;
     }
     first_read[c] = (uint32_t)lo;
+}
+
+// Window bound of many samples in one launch: block (x, s) scans reads of
+// sample s.  out[s] = {sum of max(0, len - K + 1), first offset, last offset,
+// decreasing-offsets flag}.
+struct BoundOut {
+    unsigned long long bound, first, last, bad;
+};
+__global__ void window_bound_batch_kernel(const uint64_t *const *offsets, const uint64_t *nreads,
+                                          int K, BoundOut *out) {
+    const int smp = blockIdx.y;
+    const uint64_t *off = offsets[smp];
+    const uint64_t n = nreads[smp];
+    unsigned long long sum = 0;
+    bool bad = false;
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < n;
+         r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = off[r], b = off[r + 1];
+        if (b < a) {
+            bad = true;
+            continue;
+        }
+        if (b - a >= (uint64_t)K) sum += b - a - K + 1;
+    }
+    for (int o = 16; o; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0 && sum) atomicAdd(&out[smp].bound, sum);
+    if (bad) atomicOr(&out[smp].bad, 1ull);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[smp].first = off[0];
+        out[smp].last = off[n];
+    }
+}
+
+// first_read of every sample's chunks in one launch (chunk index space as in
+// insert_batch_kernel).
+__global__ void first_read_batch_kernel(const InsertArgs *args, const unsigned long long *chunk_end,
+                                        int nsamples, unsigned long long total_chunks,
+                                        uint64_t chunk) {
+    const unsigned long long c = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    if (c >= total_chunks) return;
+    int lo = 0, hi = nsamples - 1;   // sample owning chunk c
+    while (lo < hi) {
+        const int mid = (lo + hi) / 2;
+        if (c < chunk_end[mid])
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const InsertArgs &a = args[lo];
+    const unsigned long long local = c - (lo ? chunk_end[lo - 1] : 0);
+    const uint64_t target = a.first + local * chunk;
+    uint64_t rlo = 0, rhi = a.nreads;
+    while (rlo < rhi) {
+        const uint64_t mid = rlo + (rhi - rlo) / 2;
+        if (a.offsets[mid] >= target)
+            rhi = mid;
+        else
+            rlo = mid + 1;
+    }
+    const_cast<uint32_t *>(a.first_read)[local] = (uint32_t)rlo;
 }
 
 // Re-insert keys into a distinct set (growing a set, or merging another
@@ -723,6 +818,49 @@ cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t
     if (nchunks == 0) return cudaSuccess;
     first_read_kernel<<<(unsigned)((nchunks + 255) / 256), 256, 0, s>>>(offsets, nreads, first,
                                                                          nchunks, chunk, first_read);
+    return cudaGetLastError();
+}
+
+int insert_batch_blocks_per_sm(int kw, int chunk) {
+    int n = 0;
+    if (kw == 1 && chunk == 1024)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_batch_kernel<1, 1024>, kInsertThreads, 0);
+    else if (kw == 1)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_batch_kernel<1, 2048>, kInsertThreads, 0);
+    else if (chunk == 1024)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_batch_kernel<2, 1024>, kInsertThreads, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_batch_kernel<2, 2048>, kInsertThreads, 0);
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_window_bound_batch(const uint64_t *const *offsets, const uint64_t *nreads,
+                                      int n, int K, void *out, uint64_t max_reads, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, (size_t)n * sizeof(BoundOut), s);
+    if (e != cudaSuccess || n == 0) return e;
+    uint64_t bx = (max_reads + 255) / 256;
+    if (bx > 256) bx = 256;
+    if (bx == 0) bx = 1;
+    window_bound_batch_kernel<<<dim3((unsigned)bx, (unsigned)n), 256, 0, s>>>(offsets, nreads, K,
+                                                                              (BoundOut *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_insert_batch(const InsertArgs *args, const unsigned long long *chunk_end,
+                                int nsamples, unsigned long long total_chunks, int kw, int chunk,
+                                int grid, cudaStream_t s) {
+    if (total_chunks == 0) return cudaSuccess;
+    first_read_batch_kernel<<<(unsigned)((total_chunks + 255) / 256), 256, 0, s>>>(
+        args, chunk_end, nsamples, total_chunks, (uint64_t)chunk);
+    const unsigned g = (unsigned)(total_chunks < (unsigned long long)grid ? total_chunks : grid);
+    if (kw == 1 && chunk == 1024)
+        insert_batch_kernel<1, 1024><<<g, kInsertThreads, 0, s>>>(args, chunk_end, nsamples, total_chunks);
+    else if (kw == 1)
+        insert_batch_kernel<1, 2048><<<g, kInsertThreads, 0, s>>>(args, chunk_end, nsamples, total_chunks);
+    else if (chunk == 1024)
+        insert_batch_kernel<2, 1024><<<g, kInsertThreads, 0, s>>>(args, chunk_end, nsamples, total_chunks);
+    else
+        insert_batch_kernel<2, 2048><<<g, kInsertThreads, 0, s>>>(args, chunk_end, nsamples, total_chunks);
     return cudaGetLastError();
 }
 

@@ -67,11 +67,39 @@ struct Geometry {
     uint64_t words;      // m / eta
     uint64_t m_mask;     // m - 1 when m is a power of two, else 0
     uint64_t maxc;       // 2^alpha - 1
+    uint64_t dim_x;      // two-dimensional countBF of dim_x x dim_y cells; 0: flat
+    uint64_t dim_y;
+    uint64_t mag_m, mag_x, mag_y, mag_eta;   // floor((2^64 - 1) / d) of m, dim_x, dim_y, eta
     int alpha;
     int eta;
     int eta_log2;        // log2(eta) when eta is a power of two, else -1
     int nhash;
 };
+
+// Geometry of a countBF of `words` cells (flat: dim_x == 0) or of
+// dim_x * dim_y cells (two-dimensional).  Host side; cells left NULL.
+inline Geometry make_geometry(uint64_t words, uint64_t dim_x, uint64_t dim_y, int alpha,
+                              int nhash) {
+    Geometry G;
+    G.cells = nullptr;
+    G.alpha = alpha;
+    G.eta = 64 / alpha;
+    G.nhash = nhash;
+    G.dim_x = dim_x;
+    G.dim_y = dim_x ? dim_y : 0;
+    G.words = dim_x ? dim_x * dim_y : words;
+    G.m = G.words * (uint64_t)G.eta;
+    G.m_mask = (G.m & (G.m - 1)) == 0 ? G.m - 1 : 0;
+    G.maxc = (1ull << alpha) - 1;
+    G.eta_log2 = -1;
+    for (int b = 0; b < 7; ++b)
+        if ((1 << b) == G.eta) G.eta_log2 = b;
+    G.mag_m = ~0ull / G.m;
+    G.mag_x = dim_x ? ~0ull / dim_x : 0;
+    G.mag_y = dim_x ? ~0ull / dim_y : 0;
+    G.mag_eta = ~0ull / (uint64_t)G.eta;
+    return G;
+}
 
 // ------------------------------------------------------------ hash family
 // H_a(x) = MurmurHash3_x64_128(bytes(x), seed = a).h1 (Appleby's published
@@ -140,20 +168,40 @@ __device__ __forceinline__ void murmur16(uint64_t lo, uint64_t hi, uint32_t seed
     o2 = h2;
 }
 
-// Counter index g = h mod m (flat form of Algorithm 3's i, j, l addressing).
-__device__ __forceinline__ uint64_t counter_of(const Geometry &G, uint64_t h) {
-    return G.m_mask ? (h & G.m_mask) : (h % G.m);
+// h mod d by Barrett reduction with magic = floor((2^64 - 1) / d): the
+// quotient estimate floor(h * magic / 2^64) is the true quotient or one less
+// (h * magic / 2^64 lies in (h/d - 1, h/d]), so one conditional subtraction
+// leaves the exact remainder.  Valid for every d >= 1 and every 64-bit h.
+__device__ __forceinline__ uint64_t mod_by(uint64_t h, uint64_t d, uint64_t magic) {
+    const uint64_t r = h - __umul64hi(h, magic) * d;
+    return r >= d ? r - d : r;
 }
 
-// Cell and bit shift of counter g: cell g / eta, bits alpha * (g mod eta).
-__device__ __forceinline__ void locate(const Geometry &G, uint64_t g, uint64_t &cell,
-                                       unsigned &shift) {
+// Cell and counter of hash value h (Algorithm 3's addressing).
+//   flat:              g = h mod m, cell g / eta, counter g mod eta;
+//   two-dimensional:   i = h mod x, j = h mod y, l = h mod eta, cell (i, j)
+//                      stored row-major at i * y + j, counter l.
+__device__ __forceinline__ void address(const Geometry &G, uint64_t h, uint64_t &cell,
+                                        unsigned &slot) {
+    if (G.dim_x) {
+        cell = mod_by(h, G.dim_x, G.mag_x) * G.dim_y + mod_by(h, G.dim_y, G.mag_y);
+        slot = G.eta_log2 >= 0 ? (unsigned)(h & (uint64_t)(G.eta - 1))
+                               : (unsigned)mod_by(h, (uint64_t)G.eta, G.mag_eta);
+        return;
+    }
+    const uint64_t g = G.m_mask ? (h & G.m_mask) : mod_by(h, G.m, G.mag_m);
     if (G.eta_log2 >= 0) {
         cell = g >> G.eta_log2;
-        shift = (unsigned)(g & (uint64_t)(G.eta - 1)) * (unsigned)G.alpha;
+        slot = (unsigned)(g & (uint64_t)(G.eta - 1));
     } else {
-        cell = g / (uint64_t)G.eta;
-        shift = (unsigned)(g - cell * (uint64_t)G.eta) * (unsigned)G.alpha;
+        uint64_t q = __umul64hi(g, G.mag_eta);
+        uint64_t r = g - q * (uint64_t)G.eta;
+        if (r >= (uint64_t)G.eta) {
+            r -= (uint64_t)G.eta;
+            ++q;
+        }
+        cell = q;
+        slot = (unsigned)r;
     }
 }
 
@@ -241,6 +289,18 @@ cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t
 cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s);
 int insert_blocks_per_sm(int kw, bool partitioned);
 cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s);
+
+// Batched insertion (atomic design): many samples, each with its own
+// InsertArgs (device array), chunks of all samples in one index space with
+// chunk_end[s] = chunks of samples 0..s.  Launches the batched first_read
+// kernel and the persistent insert kernel.
+constexpr int kBoundOutWords = 4;   // per-sample output of launch_window_bound_batch
+int insert_batch_blocks_per_sm(int kw, int chunk);
+cudaError_t launch_window_bound_batch(const uint64_t *const *offsets, const uint64_t *nreads,
+                                      int n, int K, void *out, uint64_t max_reads, cudaStream_t s);
+cudaError_t launch_insert_batch(const InsertArgs *args, const unsigned long long *chunk_end,
+                                int nsamples, unsigned long long total_chunks, int kw, int chunk,
+                                int grid, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
 // Insert n keys into a distinct set; when dlist is not null, keys new to the
 // set are appended to it (ctr->distinct counts them).

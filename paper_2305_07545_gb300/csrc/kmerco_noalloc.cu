@@ -163,18 +163,8 @@ extern "C" int kmerco_classify_noalloc(const uint64_t *cells, uint64_t m, int k,
     int status = scratch_on_current_device(&scratch);
     if (status != KMERCO_OK) return status;
 
-    Geometry G;
+    Geometry G = make_geometry(m / eta, 0, 0, counter_bits, nhash);
     G.cells = const_cast<uint64_t *>(cells);
-    G.m = m;
-    G.words = m / eta;
-    G.m_mask = (m & (m - 1)) == 0 ? m - 1 : 0;
-    G.maxc = maxc;
-    G.alpha = counter_bits;
-    G.eta = (int)eta;
-    G.eta_log2 = -1;
-    for (int b = 0; b < 7; ++b)
-        if ((1 << b) == (int)eta) G.eta_log2 = b;
-    G.nhash = nhash;
     const int kw = k <= 32 ? 1 : 2;
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t ntiles = (n + kTile - 1) / kTile;

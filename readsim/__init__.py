@@ -22,8 +22,9 @@ Illumina-like reads, both strands, substitution/indel errors, N calls):
               2^28 4-bit counters (128 MiB), 4 hashes, tau=3.
 ``repeats``   100 Mb uniform genome, 10% of it overwritten by repeat families
               (500-5,000 bp, 2-200 copies, 1% divergence per copy),
-              20,000,000 reads x 150 bp, 1% substitutions; K=31 or 55, 2^33
+              20,000,000 reads x 150 bp, 1% substitutions; K=31, 2^33
               4-bit counters (4 GiB), 4 hashes, tau=3.
+``repeats55`` the same reads counted as 55-mers (two-word keys).
 """
 from __future__ import annotations
 
@@ -207,6 +208,11 @@ WORKLOADS = {
                         reads=ReadModel(20_000_000, 150, sub=0.01), seed=3001,
                         repeats=dict(fraction=0.10, len_lo=500, len_hi=5000, copies_lo=2,
                                      copies_hi=200, divergence=0.01)),
+    "repeats55": Workload("repeats55", K=55, m=1 << 33, alpha=4, nhash=4, tau=3,
+                          genome_len=100_000_000, gc=0.5,
+                          reads=ReadModel(20_000_000, 150, sub=0.01), seed=3001,
+                          repeats=dict(fraction=0.10, len_lo=500, len_hi=5000, copies_lo=2,
+                                       copies_hi=200, divergence=0.01)),
 }
 
 

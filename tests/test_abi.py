@@ -79,3 +79,26 @@ def test_partitioned_mode_limits(lib, k, m, nhash):
     with pytest.raises(kc.KmercoError) as e:
         kc.kmerco_create_ex(21, 1 << 20, 4, 3, 2, update_mode=3)
     assert e.value.status == kc.EINVAL
+
+
+@pytest.mark.parametrize("dims", [(0, 5), (5, 0), ((1 << 24) + 1, 3), (3, (1 << 24) + 1)])
+def test_two_dimensional_geometry_limits(lib, dims):
+    # both dimensions 1..2^24, or both zero for a flat countBF; checked
+    # before any GPU work
+    with pytest.raises(kc.KmercoError) as e:
+        kc.kmerco_create_ex(21, 1 << 20, 4, 3, 2, dims=dims)
+    assert e.value.status == kc.EINVAL
+    with pytest.raises(kc.KmercoError) as e:   # 2^26 + cells: too many for the partitioned design
+        kc.kmerco_create_ex(21, 0, 4, 3, 2, update_mode=kc.UPDATE_PARTITIONED, dims=(8209, 8219))
+    assert e.value.status == kc.EINVAL
+
+
+def test_paper_dims_entry_point_matches_the_oracle(lib):
+    import oracle
+    for n in [1, 2, 50, 1000, 123457, 10 ** 6, 20506529, 81936236, 163872472, 10 ** 9]:
+        for fpp in (0.001, 0.01, 1e-6):
+            assert kc.kmerco_paper_dims(n, fpp) == oracle.paper_dims(n, fpp), (n, fpp)
+    for n, fpp in [(0, 0.001), (10, 0.0), (10, 1.0), (10, -1.0), (10 ** 18, 1e-9)]:
+        with pytest.raises(kc.KmercoError) as e:
+            kc.kmerco_paper_dims(n, fpp)
+        assert e.value.status == kc.EINVAL

@@ -1,0 +1,115 @@
+"""Batched insertion: many samples, each with its own countBF, in one launch.
+
+Each sample's results must equal the oracle's for that sample alone.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import readsim
+
+torch = pytest.importorskip("torch")
+import paper_2305_07545_gb300 as kc  # noqa: E402
+from test_gpu_parity import check  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _samples():
+    """Uneven samples: sizes, geometries and content differ; one is empty."""
+    out = []
+    for i in range(10):
+        n = [0, 1, 7, 50, 300, 900, 2000, 120, 4000, 33][i]
+        if n == 0:
+            b, o = readsim.from_strings([])
+        elif i == 2:
+            b, o = readsim.from_strings(["ACGTACGTAC", "AC", "ACGTNACGTACGTACGTACGTACGTACG"] * 3)
+            o = o[:n + 1] if len(o) > n + 1 else o
+        else:
+            b, o = readsim.random_reads(n, 0, 200, seed=900 + i, alphabet=b"ACGTacgtN",
+                                        weights=[24, 24, 24, 24, 1, 1, 1, 1, 0.2])
+        m = [1 << 12, 1000, 1 << 16, 4099, 1 << 20, 1 << 18, 1 << 22, 777, 1 << 24, 1 << 14][i]
+        alpha = [4, 4, 8, 5, 4, 4, 4, 16, 4, 2][i]
+        nhash = [3, 4, 1, 2, 4, 3, 4, 2, 4, 6][i]
+        out.append((b, o, m, alpha, nhash, 2 if alpha > 2 else 1))
+    return out
+
+
+def _dev(a):
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda() if len(a) else \
+        torch.zeros(1, dtype=torch.uint8 if a.dtype == np.uint8 else torch.int64, device="cuda")
+    return t
+
+
+def _run_batch(samples, K, stream, reset_twice=False, accumulate=False):
+    filters = [kc.CountBF(K, m, alpha, nhash, tau, stream=stream.cuda_stream)
+               for (_, _, m, alpha, nhash, tau) in samples]
+    dev = [(_dev(b), _dev(o)) for (b, o, *_rest) in samples]
+    torch.cuda.synchronize()
+    nreads = [len(o) - 1 for (_, o, *_r) in samples]
+    with kc.Batch(filters) as batch:
+        kc.kmerco_batch_insert(batch.b, [d[0] if n else None for d, n in zip(dev, nreads)],
+                               [d[1] for d in dev], nreads, reset=not accumulate)
+        if reset_twice or accumulate:
+            kc.kmerco_batch_insert(batch.b, [d[0] if n else None for d, n in zip(dev, nreads)],
+                                   [d[1] for d in dev], nreads, reset=not accumulate)
+        batch.classify()
+        info = batch.info()
+    results = []
+    for f in filters:
+        keys, est = f.distinct()
+        results.append(dict(stats=f.stats(), counters=f.counters(), keys=keys, est=est,
+                            trusted=f.trusted(), erroneous=f.erroneous()))
+        f.close()
+    return results, info
+
+
+@pytest.mark.parametrize("K", [21, 40])
+def test_batch_matches_oracle_per_sample(K):
+    samples = _samples()
+    stream = torch.cuda.Stream()
+    results, info = _run_batch(samples, K, stream)
+    assert info["samples"] == len(samples) and info["tuned"] == 1
+    assert info["chunk"] in (1024, 2048) and info["blocks_per_sm"] >= 2
+    for (b, o, m, alpha, nhash, tau), g in zip(samples, results):
+        check(g, b, o, K, alpha, nhash, tau)
+
+
+def test_batch_graph_replay_gives_the_same_results():
+    samples = _samples()
+    stream = torch.cuda.Stream()
+    once, _ = _run_batch(samples, 21, stream)
+    twice, info = _run_batch(samples, 21, stream, reset_twice=True)
+    assert info["graph"] == 1
+    for a, b in zip(once, twice):
+        for k in ("counters", "keys", "est", "trusted", "erroneous"):
+            assert np.array_equal(a[k], b[k]), k
+
+
+def test_batch_without_reset_accumulates():
+    samples = _samples()[3:7]
+    stream = torch.cuda.Stream()
+    results, _ = _run_batch(samples, 21, stream, accumulate=True)
+    for (b, o, m, alpha, nhash, tau), g in zip(samples, results):
+        b2 = np.concatenate([b, b])
+        o2 = np.concatenate([o, o[1:] + o[-1]])
+        check(g, b2, o2, 21, alpha, nhash, tau)
+
+
+def test_batch_rejects_bad_arguments():
+    stream = torch.cuda.Stream()
+    a = kc.CountBF(21, 1 << 12, 4, 3, 2, stream=stream.cuda_stream)
+    b = kc.CountBF(31, 1 << 12, 4, 3, 2, stream=stream.cuda_stream)
+    c = kc.CountBF(21, 1 << 12, 4, 3, 2)   # its own stream
+    for hs in ([a, b], [a, c], [a, a]):
+        with pytest.raises(kc.KmercoError) as e:
+            kc.Batch(hs)
+        assert e.value.status == kc.EINVAL
+    bases, offs = readsim.random_reads(10, 50, 60, seed=1)
+    with kc.Batch([a]) as batch, pytest.raises(kc.KmercoError) as e:
+        batch.insert([bases], [offs])   # host pointers
+    assert e.value.status == kc.EINVAL
+    for f in (a, b, c):
+        f.close()

@@ -25,9 +25,9 @@ def _dev(a: np.ndarray):
 
 
 def gpu_run(bases, offsets, K, m, alpha, nhash, tau, device_inputs=True, forward_only=False,
-            batches=None, update_mode=0):
+            batches=None, update_mode=0, dims=None):
     with kc.CountBF(K, m, alpha, nhash, tau, forward_only=forward_only,
-                    update_mode=update_mode) as bf:
+                    update_mode=update_mode, dims=dims) as bf:
         parts = batches or [(bases, offsets)]
         for b, o in parts:
             if device_inputs:
@@ -49,7 +49,9 @@ def _split_keys(keys, K):
 def check(g, bases, offsets, K, alpha, nhash, tau, forward_only=False):
     st = g["stats"]
     m = st["m_actual"]
-    ref = oracle.run(bases, offsets, K, m, alpha, nhash, tau, canonical=not forward_only)
+    dims = (st["dim_x"], st["dim_y"]) if st["dim_x"] else None
+    ref = oracle.run(bases, offsets, K, m, alpha, nhash, tau, canonical=not forward_only,
+                     dims=dims)
     assert np.array_equal(g["counters"], ref.filter), "countBF cells"
     hi, lo = _split_keys(g["keys"], K)
     assert np.array_equal(lo, ref.distinct_lo) and np.array_equal(hi, ref.distinct_hi), "distinct"
