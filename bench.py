@@ -260,7 +260,7 @@ def run_ours(args) -> None:
 
     ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    insert_ms = []
+    insert_ms, classify_ms = [], []
     launches = 0
     torch.cuda.synchronize()
     if world > 1:
@@ -275,6 +275,7 @@ def run_ours(args) -> None:
             s = bf.stats()
             launches += s["launches"] - l0 - 1   # the stats call itself launches one kernel
             insert_ms.append(s["insert_ms"])
+            classify_ms.append(s["classify_ms"])
             assert (s["inserted"], s["distinct"], s["trustworthy"]) == (inserted, distinct, trusted)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev_s, ev_e)]
@@ -353,6 +354,10 @@ def run_ours(args) -> None:
                        "l2": "256 MiB buffer written between timed steps, outside the "
                              "per-step CUDA events; countBF 128 MiB + distinct set > L2"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "phases": {"insert_ms": statistics.mean(insert_ms),
+                       "classify_ms": statistics.mean(classify_ms),
+                       "insert_kmers_per_s": inserted / (statistics.mean(insert_ms) / 1000.0),
+                       "classify_distinct_per_s": distinct / (statistics.mean(classify_ms) / 1000.0)},
             "gpu_launches": launches, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     if world > 1:

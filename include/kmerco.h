@@ -73,7 +73,7 @@ typedef struct {
     int update_mode;       /* how counter increments reach the countBF (same result either way):
                               0 automatic; 1 atomic compare-and-swap on each 64-bit cell;
                               2 partitioned: increments grouped by countBF slice and applied in
-                              shared memory (needs k <= 32, nhash <= 4, at most 2^26 cells;
+                              shared memory (needs nhash <= 4 and at most 2^30 cells;
                               otherwise create returns EINVAL) */
     uint64_t dim_x;        /* two-dimensional countBF (Section 2.1, Algorithm 3): dim_x x dim_y
                               cells of eta counters; m is then ignored and m_actual is
@@ -83,6 +83,19 @@ typedef struct {
                               Both 0: flat countBF of m counters.  Otherwise both 1..2^24;
                               the paper takes primes from Eq. 1 (kmerco_paper_dims). */
     uint64_t dim_y;
+    int canonical_hash;    /* 1: the canonical K-mer is the strand with the smaller H_0 hash
+                              (Section 2.3's equation with h = H_0; equal hashes take the
+                              reverse complement); 0: the smaller packed value, i.e. the
+                              lexicographically smaller strand (default).  Needs
+                              forward_only == 0. */
+    int whole_file;        /* 1: the reads of one kmerco_insert call are taken as one sequence
+                              and windows run across read boundaries (a window spanning the
+                              end of one read and the start of the next is counted); 0:
+                              windows stay inside reads (default). */
+    uint64_t pass_codes;   /* partitioned design: counter increments staged per pass, 1..2^31;
+                              0: 2^31.  A batch with more increments is inserted in several
+                              passes over consecutive parts of its reads; smaller values bound
+                              the scratch memory (about 10 bytes per staged increment). */
 } kmerco_config_t;
 
 /* Running totals and results of one handle (kmerco_stats). */

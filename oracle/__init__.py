@@ -104,6 +104,13 @@ def lib() -> ctypes.CDLL:
                                          ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_uint64, _u64p, _u8p]
         L.oracle_classify_2d.restype = ctypes.c_uint64
+        L.oracle_extract_ex.argtypes = [_u8p, _u64p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _u64p, _u64p, _u64p, _u64p]
+        L.oracle_extract_ex.restype = ctypes.c_uint64
+        L.oracle_literal_insertion.argtypes = [_u8p, _u64p, ctypes.c_uint64, ctypes.c_int,
+                                               ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                               ctypes.c_int, ctypes.c_int, _u64p, _u64p, _u64p]
+        L.oracle_literal_insertion.restype = ctypes.c_uint64
         L.oracle_paper_dims.argtypes = [ctypes.c_uint64, ctypes.c_double, _u64p, _u64p]
         L.oracle_paper_dims.restype = ctypes.c_int
         L.oracle_merge.restype = None
@@ -171,22 +178,32 @@ class Extracted:
         return len(self.lo)
 
 
-def extract(bases: np.ndarray, offsets: np.ndarray, K: int, canonical: bool = True) -> Extracted:
-    """All valid windows of all reads, in input order (Algorithm 1 loop)."""
+def extract(bases: np.ndarray, offsets: np.ndarray, K: int, canonical: bool = True,
+            canonical_hash: bool = False, whole_file: bool = False) -> Extracted:
+    """All valid windows of all reads, in input order (Algorithm 1 loop).
+
+    ``canonical_hash`` picks the strand with the smaller H_0 instead of the
+    lexicographically smaller one; ``whole_file`` runs the windows across
+    read boundaries (the reads as one sequence).
+    """
     bases = np.ascontiguousarray(bases, dtype=np.uint8)
     offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
     nreads = len(offsets) - 1
     if nreads < 0:
         raise ValueError("offsets needs nreads + 1 entries")
+    if canonical_hash and not canonical:
+        raise ValueError("canonical_hash needs canonical K-mers")
     cap = int(sum(max(0, int(offsets[r + 1]) - int(offsets[r]) - K + 1) for r in range(nreads))) \
-        if nreads < 4096 else int(max(0, int(offsets[-1]) - int(offsets[0])))
+        if nreads < 4096 and not whole_file else int(max(0, int(offsets[-1]) - int(offsets[0])))
     hi = np.zeros(max(cap, 1), np.uint64)
     lo = np.zeros(max(cap, 1), np.uint64)
     nw = ctypes.c_uint64(0)
     ns = ctypes.c_uint64(0)
     bptr = bases if len(bases) else np.zeros(1, np.uint8)
-    n = lib().oracle_extract(_p(bptr, _u8p), _p(offsets, _u64p), nreads, K, int(canonical),
-                             _p(hi, _u64p), _p(lo, _u64p), ctypes.byref(nw), ctypes.byref(ns))
+    mode = 2 if canonical_hash else int(bool(canonical))
+    n = lib().oracle_extract_ex(_p(bptr, _u8p), _p(offsets, _u64p), nreads, K, mode,
+                                int(bool(whole_file)), _p(hi, _u64p), _p(lo, _u64p),
+                                ctypes.byref(nw), ctypes.byref(ns))
     return Extracted(hi[:n].copy(), lo[:n].copy(), int(nw.value), int(ns.value))
 
 
@@ -298,6 +315,29 @@ def classify_2d(filt: np.ndarray, dhi: np.ndarray, dlo: np.ndarray, K: int,
     return est[:d].copy(), tr[:d].astype(bool)
 
 
+def literal_insertion(bases: np.ndarray, offsets: np.ndarray, K: int, m: int, alpha: int,
+                      nhash: int, dims: tuple[int, int] | None = None):
+    """Algorithms 1, 3 and 4 exactly as printed, in input order (diagnostic).
+
+    Returns (filter, first-seen keys as (hi, lo) arrays).  Order dependent:
+    the strand and the early overflow stop depend on the filter state.
+    """
+    bases = np.ascontiguousarray(bases, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+    nreads = len(offsets) - 1
+    dx, dy = dims if dims is not None else (0, 0)
+    words_ = dx * dy if dims is not None else words(m, alpha)
+    filt = np.zeros(max(words_, 1), np.uint64)
+    cap = max(1, int(offsets[-1] - offsets[0]) if nreads > 0 else 1)
+    dhi = np.zeros(cap, np.uint64)
+    dlo = np.zeros(cap, np.uint64)
+    bptr = bases if len(bases) else np.zeros(1, np.uint8)
+    n = lib().oracle_literal_insertion(_p(bptr, _u8p), _p(offsets, _u64p), nreads, K, m, dx, dy,
+                                       alpha, nhash, _p(filt, _u64p), _p(dhi, _u64p),
+                                       _p(dlo, _u64p))
+    return filt[:words_], dhi[:n].copy(), dlo[:n].copy()
+
+
 def merge(dst: np.ndarray, src: np.ndarray, m: int, alpha: int) -> np.ndarray:
     """Counter-wise saturating sum of two filters, in place in ``dst``."""
     lib().oracle_merge(_p(dst, _u64p), _p(np.ascontiguousarray(src, np.uint64), _u64p), m, alpha)
@@ -319,7 +359,8 @@ class Result:
 
 def run(bases: np.ndarray, offsets: np.ndarray, K: int, m: int, alpha: int, nhash: int,
         tau: int, canonical: bool = True, cross_check: bool = True,
-        with_counts: bool = False, dims: tuple[int, int] | None = None) -> Result:
+        with_counts: bool = False, dims: tuple[int, int] | None = None,
+        canonical_hash: bool = False, whole_file: bool = False) -> Result:
     """The whole path: extract -> countBF -> distinct -> classify.
 
     With ``cross_check`` the filter is built both by the closed form and by
@@ -328,14 +369,14 @@ def run(bases: np.ndarray, offsets: np.ndarray, K: int, m: int, alpha: int, nhas
     closed form exists for the flat layout only, so there is no cross-check).
     """
     if dims is not None:
-        ex = extract(bases, offsets, K, canonical)
+        ex = extract(bases, offsets, K, canonical, canonical_hash, whole_file)
         filt = insert_sequential_2d(ex.hi, ex.lo, K, dims, alpha, nhash)
         dhi, dlo, cnt = distinct(ex.hi, ex.lo)
         est, tr = classify_2d(filt, dhi, dlo, K, dims, alpha, nhash, tau)
         return Result(filt, dhi, dlo, est, tr, ex.n_windows, ex.n_skipped, ex.n,
                       cnt if with_counts else None)
     _check_params(K, m, alpha, nhash)
-    ex = extract(bases, offsets, K, canonical)
+    ex = extract(bases, offsets, K, canonical, canonical_hash, whole_file)
     filt = insert_sequential(ex.hi, ex.lo, K, m, alpha, nhash)
     if cross_check:
         cf = counters_closed_form(ex.hi, ex.lo, K, m, alpha, nhash)

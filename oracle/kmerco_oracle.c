@@ -159,28 +159,41 @@ static int u128_less(uint64_t ahi, uint64_t alo, uint64_t bhi, uint64_t blo)
     return ahi < bhi || (ahi == bhi && alo < blo);
 }
 
+uint64_t oracle_kmer_hash(int K, uint64_t hi, uint64_t lo, uint32_t a);
+
 /*
  * Window extraction (Section 1.1 / Fig. 1: a sequence of length len has
  * len-K+1 K-mers; Algorithm 1 takes each in turn), reverse complement and
  * canonical choice (Section 2.3).
  *
  * Reads are CSR: read r is bases[offsets[r] .. offsets[r+1]).  Every window
- * of K consecutive bases inside one read is visited in input order; a
- * window with any non-ACGT byte is skipped and counted in *n_skipped.  For
- * each valid window the canonical key (or the forward key when
- * canonical == 0) is written to hi[n], lo[n] when those are non-NULL.
- * *n_windows receives sum over reads of max(0, len-K+1).  Returns the number
- * of valid windows.
+ * of K consecutive bases inside one read is visited in input order; with
+ * whole_file != 0 the reads are instead taken as one sequence
+ * bases[offsets[0] .. offsets[nreads]) and windows run across read
+ * boundaries (the reading under which the paper's 55-mer totals are its
+ * 28-mer totals minus 27).  A window with any non-ACGT byte is skipped and
+ * counted in *n_skipped.  For each valid window the key is written to
+ * hi[n], lo[n] when those are non-NULL:
+ *   canonical == 0  the forward K-mer as read;
+ *   canonical == 1  the smaller of forward and reverse complement as packed
+ *                   integers (lexicographic, A < C < G < T);
+ *   canonical == 2  the strand with the smaller hash H_0 -- Section 2.3's
+ *                   equation with h = H_0: forward when
+ *                   H_0(forward) < H_0(reverse complement), else the
+ *                   reverse complement.
+ * *n_windows receives the number of windows (sum over reads of
+ * max(0, len-K+1)).  Returns the number of valid windows.
  */
-uint64_t oracle_extract(const uint8_t *bases, const uint64_t *offsets,
-                        uint64_t nreads, int K, int canonical,
-                        uint64_t *hi, uint64_t *lo,
-                        uint64_t *n_windows, uint64_t *n_skipped)
+uint64_t oracle_extract_ex(const uint8_t *bases, const uint64_t *offsets,
+                           uint64_t nreads, int K, int canonical, int whole_file,
+                           uint64_t *hi, uint64_t *lo,
+                           uint64_t *n_windows, uint64_t *n_skipped)
 {
     int codes[64], rc[64];
     uint64_t n = 0, windows = 0, skipped = 0;
-    for (uint64_t r = 0; r < nreads; ++r) {
-        uint64_t start = offsets[r], end = offsets[r + 1];
+    uint64_t nseq = whole_file ? (nreads > 0) : nreads;
+    for (uint64_t r = 0; r < nseq; ++r) {
+        uint64_t start = offsets[r], end = whole_file ? offsets[nreads] : offsets[r + 1];
         if (end < start + (uint64_t)K) continue;
         for (uint64_t p = start; p + (uint64_t)K <= end; ++p) {
             ++windows;
@@ -196,7 +209,10 @@ uint64_t oracle_extract(const uint8_t *bases, const uint64_t *offsets,
             if (canonical) {
                 reverse_complement_codes(codes, K, rc);
                 pack_codes(rc, K, &rh, &rl);
-                if (u128_less(rh, rl, fh, fl)) { kh = rh; kl = rl; }
+                int take_rc = canonical == 2
+                    ? !(oracle_kmer_hash(K, fh, fl, 0) < oracle_kmer_hash(K, rh, rl, 0))
+                    : u128_less(rh, rl, fh, fl);
+                if (take_rc) { kh = rh; kl = rl; }
             }
             if (hi) hi[n] = kh;
             if (lo) lo[n] = kl;
@@ -206,6 +222,16 @@ uint64_t oracle_extract(const uint8_t *bases, const uint64_t *offsets,
     if (n_windows) *n_windows = windows;
     if (n_skipped) *n_skipped = skipped;
     return n;
+}
+
+/* Windows inside reads; canonical 0 (forward) or 1 (lexicographic). */
+uint64_t oracle_extract(const uint8_t *bases, const uint64_t *offsets,
+                        uint64_t nreads, int K, int canonical,
+                        uint64_t *hi, uint64_t *lo,
+                        uint64_t *n_windows, uint64_t *n_skipped)
+{
+    return oracle_extract_ex(bases, offsets, nreads, K, canonical, 0, hi, lo, n_windows,
+                             n_skipped);
 }
 
 /*
@@ -523,4 +549,95 @@ int oracle_paper_dims(uint64_t n, double fpp, uint64_t *X, uint64_t *Y)
     *X = x;
     *Y = y;
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 as printed (diagnostic; not a parity target)                 */
+/* ------------------------------------------------------------------------ */
+
+/* Packed value of K codes read from ASCII bases (all valid). */
+static void pack_bases(const uint8_t *p, int K, int rc, uint64_t *hi, uint64_t *lo)
+{
+    int codes[64], r[64];
+    for (int i = 0; i < K; ++i) codes[i] = oracle_base_code(p[i]);
+    if (rc) {
+        reverse_complement_codes(codes, K, r);
+        pack_codes(r, K, hi, lo);
+    } else {
+        pack_codes(codes, K, hi, lo);
+    }
+}
+
+/*
+ * The insertion phase exactly as Algorithms 1, 3 and 4 print it, in input
+ * order, with the paper's state-dependent choices kept:
+ *   QcountBF-I (Algorithm 4): for a = 1..k_h compare H_a(Read) with
+ *     H_a(Read_RC); Result = 0 when H_a(Read) < H_a(Read_RC), else 1; read
+ *     the counter of the smaller hash and return 0 at once when it is 0;
+ *     otherwise the minimum.  Result is the one of the last iteration run.
+ *   Algorithm 1: the strand Result names is inserted; when the query
+ *     returned 0 it is also appended to the distinct list (first seen).
+ *   IcountBF (Algorithm 3): for a = 1..k_h the counter of H_a(key) is
+ *     incremented, and the whole insertion stops at the first counter
+ *     that cannot take one more (value + 1 > 2^alpha - 1; "Counter
+ *     Overflow, return").
+ * Hash index a = 1..k_h is seed a - 1 (the seeds of H_a elsewhere).
+ * Flat (dx == 0, m counters) or two-dimensional (dx x dy cells) geometry.
+ * Windows stay inside reads; windows with non-ACGT bytes are skipped.
+ * Keys appended to the distinct list go to dhi/dlo (may be NULL).  Returns
+ * the number of first-seen windows.
+ */
+uint64_t oracle_literal_insertion(const uint8_t *bases, const uint64_t *offsets,
+                                  uint64_t nreads, int K, uint64_t m, uint64_t dx,
+                                  uint64_t dy, int alpha, int nhash, uint64_t *filter,
+                                  uint64_t *dhi, uint64_t *dlo)
+{
+    uint64_t maxc = (1ULL << alpha) - 1, first_seen = 0;
+    for (uint64_t r = 0; r < nreads; ++r) {
+        for (uint64_t p = offsets[r]; p + (uint64_t)K <= offsets[r + 1]; ++p) {
+            int ok = 1;
+            for (int i = 0; i < K; ++i)
+                if (oracle_base_code(bases[p + i]) < 0) ok = 0;
+            if (!ok) continue;
+            uint64_t fh, fl, rh, rl;
+            pack_bases(bases + p, K, 0, &fh, &fl);
+            pack_bases(bases + p, K, 1, &rh, &rl);
+            /* QcountBF-I */
+            int result = 0;
+            uint64_t freq = ~0ULL;
+            for (int a = 0; a < nhash; ++a) {
+                uint64_t h = oracle_kmer_hash(K, fh, fl, (uint32_t)a);
+                uint64_t h1 = oracle_kmer_hash(K, rh, rl, (uint32_t)a);
+                if (h < h1) {
+                    result = 0;
+                } else {
+                    h = h1;
+                    result = 1;
+                }
+                uint64_t w;
+                int l;
+                address(h, m, dx, dy, alpha, &w, &l);
+                uint64_t value = read_counter(filter, w, alpha, l);
+                if (value == 0) { freq = 0; break; }
+                if (value < freq) freq = value;
+            }
+            uint64_t kh = result ? rh : fh, kl = result ? rl : fl;
+            if (freq == 0) {
+                if (dhi) dhi[first_seen] = kh;
+                if (dlo) dlo[first_seen] = kl;
+                ++first_seen;
+            }
+            /* IcountBF */
+            for (int a = 0; a < nhash; ++a) {
+                uint64_t w;
+                int l;
+                address(oracle_kmer_hash(K, kh, kl, (uint32_t)a), m, dx, dy, alpha, &w, &l);
+                uint64_t value = read_counter(filter, w, alpha, l);
+                if (value + 1 > maxc) break; /* counter overflow: insertion ends */
+                filter[w] = (filter[w] & oracle_reset_mask(alpha, l)) |
+                            ((value + 1) << (alpha * l));
+            }
+        }
+    }
+    return first_seen;
 }

@@ -28,7 +28,8 @@ class kmerco_config_t(ctypes.Structure):
     _fields_ = [("k", c_int), ("m", c_uint64), ("counter_bits", c_int), ("nhash", c_int),
                 ("threshold", c_uint32), ("forward_only", c_int), ("stream", c_void_p),
                 ("hbm_budget", c_uint64), ("device", c_int), ("update_mode", c_int),
-                ("dim_x", c_uint64), ("dim_y", c_uint64)]
+                ("dim_x", c_uint64), ("dim_y", c_uint64), ("canonical_hash", c_int),
+                ("whole_file", c_int), ("pass_codes", c_uint64)]
 
 
 class kmerco_stats_t(ctypes.Structure):
@@ -153,10 +154,12 @@ UPDATE_AUTO, UPDATE_ATOMIC, UPDATE_PARTITIONED = 0, 1, 2
 def kmerco_create_ex(k: int, m: int, counter_bits: int, nhash: int, threshold: int,
                      forward_only: bool = False, stream: int | None = None,
                      hbm_budget: int = 0, device: int = -1, update_mode: int = 0,
-                     dims: tuple[int, int] | None = None) -> int:
+                     dims: tuple[int, int] | None = None, pass_codes: int = 0,
+                     canonical_hash: bool = False, whole_file: bool = False) -> int:
     dx, dy = dims if dims is not None else (0, 0)
     cfg = kmerco_config_t(k, m, counter_bits, nhash, threshold, int(forward_only),
-                          stream or None, hbm_budget, device, update_mode, dx, dy)
+                          stream or None, hbm_budget, device, update_mode, dx, dy,
+                          int(canonical_hash), int(whole_file), pass_codes)
     h = c_void_p()
     _check(load().kmerco_create_ex(byref(cfg), byref(h)), "kmerco_create_ex")
     return h.value
@@ -277,13 +280,15 @@ class CountBF:
     def __init__(self, k: int, m: int, counter_bits: int = 4, nhash: int = 4,
                  threshold: int = 3, forward_only: bool = False, stream: int | None = None,
                  hbm_budget: int = 0, device: int = -1, update_mode: int = UPDATE_AUTO,
-                 dims: tuple[int, int] | None = None):
+                 dims: tuple[int, int] | None = None, pass_codes: int = 0,
+                 canonical_hash: bool = False, whole_file: bool = False):
         """``dims = (X, Y)`` makes a two-dimensional countBF of X x Y cells
         (Algorithm 3's addressing; ``m`` is then ignored)."""
         self.k = k
         self.kw = 1 if k <= 32 else 2
         self.h = kmerco_create_ex(k, m, counter_bits, nhash, threshold, forward_only, stream,
-                                  hbm_budget, device, update_mode, dims)
+                                  hbm_budget, device, update_mode, dims, pass_codes,
+                                  canonical_hash, whole_file)
 
     def close(self) -> None:
         if self.h:

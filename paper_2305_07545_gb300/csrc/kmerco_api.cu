@@ -16,12 +16,14 @@
 using namespace countbf;
 
 struct kmerco {
-    int K, kw, alpha, eta, nhash, canonical;
+    int K, kw, alpha, eta, nhash, canonical;   // canonical: 0 forward, 1 lexicographic, 2 hash
+    int whole_file;
     uint32_t tau;
     int device;
     cudaStream_t stream;
     bool own_stream;
     int update_mode;         // 0 automatic, 1 atomic, 2 partitioned
+    uint64_t pass_codes;     // increments staged per partitioned pass
     int grid_atomic, grid_part;
     uint64_t budget, used;
     Geometry G;
@@ -210,11 +212,14 @@ int validate(const kmerco_config_t *c) {
     const uint64_t maxc = (1ull << c->counter_bits) - 1;
     if ((uint64_t)c->threshold >= maxc) return KMERCO_EINVAL;
     if (c->forward_only != 0 && c->forward_only != 1) return KMERCO_EINVAL;
+    if (c->canonical_hash != 0 && (c->canonical_hash != 1 || c->forward_only)) return KMERCO_EINVAL;
+    if (c->whole_file != 0 && c->whole_file != 1) return KMERCO_EINVAL;
     if (c->update_mode < 0 || c->update_mode > 2) return KMERCO_EINVAL;
+    if (c->pass_codes > kMaxBatchCodes) return KMERCO_EINVAL;
     if (c->update_mode == 2) {
         const uint64_t eta = 64 / (uint64_t)c->counter_bits;
         const uint64_t words = c->dim_x ? c->dim_x * c->dim_y : (c->m + eta - 1) / eta;
-        if (c->k > 32 || c->nhash > kPartMaxHash || words > (1ull << (kMaxCoarseShift + 6)))
+        if (c->nhash > kPartMaxHash || words > (1ull << (kMaxCoarseShift + 6)))
             return KMERCO_EINVAL;
     }
     return KMERCO_OK;
@@ -223,8 +228,7 @@ int validate(const kmerco_config_t *c) {
 // Whether this handle applies counter increments with the partitioned design.
 bool use_partitioned(const kmerco_t *h) {
     if (h->update_mode == 1) return false;
-    const bool able = h->kw == 1 && h->nhash <= kPartMaxHash &&
-                      h->G.words <= (1ull << (kMaxCoarseShift + 6));
+    const bool able = h->nhash <= kPartMaxHash && h->G.words <= (1ull << (kMaxCoarseShift + 6));
     if (h->update_mode == 2) return able;
     return able && h->G.words >= (1ull << 17);   // smaller countBFs stay L2-resident
 }
@@ -303,7 +307,8 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
     h->eta = 64 / cfg->counter_bits;
     h->nhash = cfg->nhash;
     h->tau = cfg->threshold;
-    h->canonical = cfg->forward_only ? 0 : 1;
+    h->canonical = cfg->forward_only ? 0 : cfg->canonical_hash ? 2 : 1;
+    h->whole_file = cfg->whole_file;
     h->budget = cfg->hbm_budget;
     if (cfg->device >= 0) {
         h->device = cfg->device;
@@ -331,8 +336,9 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
         if (sms <= 0) sms = 1;
         h->update_mode = cfg->update_mode;
+        h->pass_codes = cfg->pass_codes ? cfg->pass_codes : kMaxBatchCodes;
         h->grid_atomic = sms * insert_blocks_per_sm(h->kw, false);
-        h->grid_part = sms * insert_blocks_per_sm(1, true);
+        h->grid_part = sms * insert_blocks_per_sm(h->kw, true);
 
         const uint64_t eta = (uint64_t)h->eta;
         h->G = make_geometry((cfg->m + eta - 1) / eta, cfg->dim_x, cfg->dim_y, h->alpha,
@@ -444,6 +450,8 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
         bound = h->ctr_host->bound;
         d_off = offsets;
     }
+    if (h->whole_file)   // the reads are one sequence of last - first bases
+        bound = last - first >= (uint64_t)K ? last - first - K + 1 : 0;
     const uint64_t nbytes = last - first;
     if (nbytes && !bases) return KMERCO_EINVAL;
     const uint8_t *d_bases = nullptr;
@@ -460,34 +468,39 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     if (bound == 0) return KMERCO_OK;   // no window fits in any read
     KM_TRY(ensure_set_capacity(h, bound));
 
-    // Partitioned design: size the increment-code buffers for this batch (the
-    // atomic design takes over when they cannot be had).
+    // Partitioned design: size the increment-code buffers for one pass of at
+    // most kMaxBatchCodes increments; larger inputs run in several passes over
+    // consecutive chunk ranges (the atomic design takes over when the buffers
+    // cannot be had).
     bool part = use_partitioned(h);
     int coarse_shift = 0, slice_shift = 0;
-    uint64_t coarse_cap = 0, fine_cap = 0, nslices = 0;
+    uint64_t coarse_cap = 0, fine_cap = 0, nslices = 0, passes = 1;
     bool repart = false;
     if (part) {
         const uint64_t W = h->G.words, U = bound * (uint64_t)h->nhash;
+        const uint64_t part_chunks = (nbytes + kPartChunk - 1) / kPartChunk;
+        passes = (U + h->pass_codes - 1) / h->pass_codes;
+        if (passes > part_chunks) passes = part_chunks;   // a pass takes one chunk at least
+        if (passes < 1) passes = 1;
+        const uint64_t Up = (U + passes - 1) / passes;   // increments per pass, on average
         coarse_shift = ceil_log2(W) - 6;
         if (coarse_shift < 0) coarse_shift = 0;
         repart = coarse_shift > kSliceShift;
         slice_shift = repart ? kSliceShift : coarse_shift;
         nslices = (W + (1ull << slice_shift) - 1) >> slice_shift;
-        coarse_cap = U / kCoarseBins;
+        coarse_cap = Up / kCoarseBins;
         coarse_cap = (coarse_cap + coarse_cap / 6 + 4096 + 3) & ~3ull;   // multiple of 4 codes
-        fine_cap = repart ? U / nslices : 0;
+        fine_cap = repart ? Up / nslices : 0;
         fine_cap = (fine_cap + fine_cap / 5 + 1024 + 3) & ~3ull;
-        if (U > (1ull << 31) ||
-            ensure(h, &h->coarse, &h->coarse_alloc, kCoarseBins * coarse_cap) != KMERCO_OK ||
+        if (ensure(h, &h->coarse, &h->coarse_alloc, kCoarseBins * coarse_cap) != KMERCO_OK ||
             (repart && ensure(h, &h->fine, &h->fine_alloc, nslices * fine_cap) != KMERCO_OK) ||
             ensure(h, &h->part_ctr, &h->part_ctr_alloc, 2 * kCoarseBins + 2 * nslices) != KMERCO_OK)
             part = false;
-        else
-            KM_CUDA(cudaMemsetAsync(h->part_ctr, 0, (2 * kCoarseBins + 2 * nslices) * 8, h->stream));
     }
 
     const uint64_t chunk = part ? kPartChunk : kChunk;
     const uint64_t nchunks = (nbytes + chunk - 1) / chunk;
+    if (!part) passes = 1;
     KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, nchunks));
     KM_CUDA(launch_first_read(d_off, nreads, first, nchunks, chunk, h->first_read, h->stream));
     h->launches += nchunks ? 1 : 0;
@@ -499,9 +512,11 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     a.first = first;
     a.last = last;
     a.first_read = h->first_read;
+    a.chunk_begin = 0;
     a.nchunks = nchunks;
     a.K = K;
     a.canonical = h->canonical;
+    a.whole_file = h->whole_file;
     a.G = h->G;
     a.table = h->table;
     a.cap = h->cap;
@@ -515,9 +530,15 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     a.coarse_cursor = h->part_ctr;
     a.coarse_written = h->part_ctr ? h->part_ctr + kCoarseBins : nullptr;
     KM_CUDA(cudaEventRecord(h->ev[0], h->stream));
-    KM_CUDA(launch_insert(a, part ? h->grid_part : h->grid_atomic, h->stream));
-    h->launches += nchunks ? 1 : 0;
-    if (part) {
+    for (uint64_t pass = 0; pass < passes; ++pass) {
+        a.chunk_begin = nchunks * pass / passes;
+        a.nchunks = nchunks * (pass + 1) / passes;
+        if (part)
+            KM_CUDA(cudaMemsetAsync(h->part_ctr, 0, (2 * kCoarseBins + 2 * nslices) * 8,
+                                    h->stream));
+        KM_CUDA(launch_insert(a, part ? h->grid_part : h->grid_atomic, h->stream));
+        h->launches += a.nchunks > a.chunk_begin ? 1 : 0;
+        if (!part) continue;
         unsigned long long *fine_cursor = h->part_ctr + 2 * kCoarseBins;
         unsigned long long *fine_written = fine_cursor + nslices;
         if (repart) {
@@ -866,7 +887,8 @@ int batch_build_args(kmerco_batch *b, int chunk) {
         kmerco_t *h = b->h[i];
         const unsigned long long *bo = &b->bound_host[(size_t)i * kBoundOutWords];
         const uint64_t first = bo[1], last = bo[2];
-        const uint64_t nchunks = bo[0] ? (last - first + chunk - 1) / chunk : 0;
+        const bool any = h->whole_file ? last - first >= (uint64_t)h->K : bo[0] != 0;
+        const uint64_t nchunks = any ? (last - first + chunk - 1) / chunk : 0;
         InsertArgs &a = b->args[i];
         memset(&a, 0, sizeof(a));
         a.bases = (const uint8_t *)b->p_bases[i] + first;
@@ -875,9 +897,11 @@ int batch_build_args(kmerco_batch *b, int chunk) {
         a.first = first;
         a.last = last;
         a.first_read = h->first_read;
+        a.chunk_begin = 0;
         a.nchunks = nchunks;
         a.K = h->K;
         a.canonical = h->canonical;
+        a.whole_file = h->whole_file;
         a.G = h->G;
         a.table = h->table;
         a.cap = h->cap;
@@ -1039,7 +1063,10 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
         kmerco_t *h = b->h[i];
         if (reset) KM_TRY(kmerco_reset(h));
         const unsigned long long *bo = &b->bound_host[(size_t)i * kBoundOutWords];
-        KM_TRY(ensure_set_capacity(h, bo[0]));
+        uint64_t bound = bo[0];
+        if (h->whole_file)   // the sample's reads are one sequence
+            bound = bo[2] - bo[1] >= (uint64_t)h->K ? bo[2] - bo[1] - h->K + 1 : 0;
+        KM_TRY(ensure_set_capacity(h, bound));
         const uint64_t most = (bo[2] - bo[1] + 1023) / 1024;   // chunks at the smallest chunk size
         KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, most ? most : 1));
     }

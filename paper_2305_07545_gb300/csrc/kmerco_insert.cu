@@ -53,6 +53,7 @@ struct __align__(16) InsertSmem {
     // partitioned design: the chunk's counter-increment codes
     uint32_t staged[PART ? CHUNK * kPartMaxHash : 1];
     uint32_t sorted[PART ? CHUNK * kPartMaxHash : 1];
+    uint8_t sbin[PART ? CHUNK * kPartMaxHash : 1];   // coarse region of staged[i]
     unsigned hist[PART ? kCoarseBins : 1];
     unsigned start[PART ? kCoarseBins : 1];
     unsigned fill[PART ? kCoarseBins : 1];
@@ -222,8 +223,10 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
         S.pk[t ^ 1] = code;
         S.inv[t] = (uint16_t)bad;
     }
-    // 2b. read starts inside the staged span
-    for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; r < a.nreads; r += kInsertThreads) {
+    // 2b. read starts inside the staged span (none when the reads are one
+    //     sequence)
+    for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; !a.whole_file && r < a.nreads;
+         r += kInsertThreads) {
         uint64_t s = a.offsets[r] - a.first;
         if (s >= c0 + nb) break;
         if (s < c0) continue;   // only with decreasing offsets, which the host rejects
@@ -266,9 +269,15 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
             if (KW == 1) {
                 const uint64_t fwd = t0 >> (64 - 2 * K);
                 klo = fwd;
-                if (a.canonical) {
+                if (a.canonical == 1) {
                     const uint64_t rc = revcomp64(fwd, K);
                     klo = rc < fwd ? rc : fwd;
+                } else if (a.canonical == 2) {   // the strand with the smaller H_0
+                    const uint64_t rc = revcomp64(fwd, K);
+                    uint64_t hf, hr, t;
+                    murmur8(premix8(fwd), 0u, hf, t);
+                    murmur8(premix8(rc), 0u, hr, t);
+                    klo = hf < hr ? fwd : rc;
                 }
             } else {
                 const uint64_t x2 = pk64[w + 2];
@@ -287,7 +296,16 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
                 if (a.canonical) {
                     uint64_t rhi, rlo;
                     revcomp128(fhi, flo, K, rhi, rlo);
-                    if (rhi < fhi || (rhi == fhi && rlo < flo)) {
+                    bool take_rc;
+                    if (a.canonical == 2) {   // the strand with the smaller H_0
+                        uint64_t hf, hr, t;
+                        murmur16(flo, fhi, 0u, hf, t);
+                        murmur16(rlo, rhi, 0u, hr, t);
+                        take_rc = !(hf < hr);
+                    } else {
+                        take_rc = rhi < fhi || (rhi == fhi && rlo < flo);
+                    }
+                    if (take_rc) {
                         klo = rlo;
                         khi = rhi;
                     }
@@ -324,8 +342,9 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
             if (KW == 1 && a0 == 0 && active)
                 table_first = load_hint(a.table + __umul64hi(table_hash, a.cap), pol_stream);
             if (PART) {
-                // stage one 32-bit code per increment: coarse region (6 bits),
-                // cell within the region (20 bits), counter within the cell
+                // stage one 32-bit code per increment, cell within the coarse
+                // region (up to 24 bits) above the counter within the cell
+                // (6 bits); the region itself goes beside it
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const unsigned bal = __ballot_sync(0xffffffffu, use[j]);
@@ -334,9 +353,10 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
                     base = __shfl_sync(0xffffffffu, base, 0);
                     if (use[j]) {
                         const unsigned bin = (unsigned)(cell[j] >> a.coarse_shift);
-                        const uint32_t code = (bin << 26) |
+                        const unsigned at = base + __popc(bal & ((1u << lane) - 1));
+                        S.staged[at] =
                             ((uint32_t)(cell[j] & ((1ull << a.coarse_shift) - 1)) << 6) | slot[j];
-                        S.staged[base + __popc(bal & ((1u << lane) - 1))] = code;
+                        S.sbin[at] = (uint8_t)bin;
                         atomicAdd(&S.hist[bin], 1u);
                     }
                 }
@@ -397,23 +417,25 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
         }
         __syncthreads();
         for (unsigned i = tid; i < nupd; i += kInsertThreads) {
-            const uint32_t code = S.staged[i];
-            const unsigned bin = code >> 26;
-            S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = code;
+            const unsigned bin = S.sbin[i];
+            S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = S.staged[i];
         }
         __syncthreads();
-        for (unsigned i = tid; i < nupd; i += kInsertThreads) {
-            const uint32_t code = S.sorted[i];
-            const unsigned bin = code >> 26;
+        // one warp per region run: contiguous stores into the region
+        for (unsigned bin = warp; bin < kCoarseBins; bin += kInsertThreads / 32) {
+            const unsigned n = S.hist[bin], s0 = S.start[bin];
             const unsigned long long b0 = S.base[bin];
-            if (b0 != ~0ull) {
-                a.coarse[(uint64_t)bin * a.coarse_cap + b0 + (i - S.start[bin])] = code;
-            } else {
-                const uint64_t cell = ((uint64_t)bin << a.coarse_shift) |
-                                      ((code >> 6) & ((1u << a.coarse_shift) - 1));
-                const unsigned shift = (code & 63u) * (unsigned)G.alpha;
-                sat_increment(G.cells, cell, shift, G.maxc, load_cg(G.cells + cell),
-                              &a.ctr->error);
+            uint32_t *dst = b0 != ~0ull ? a.coarse + (uint64_t)bin * a.coarse_cap + b0 : nullptr;
+            for (unsigned i = lane; i < n; i += 32) {
+                const uint32_t code = S.sorted[s0 + i];
+                if (dst) {
+                    dst[i] = code;
+                } else {
+                    const uint64_t cell = ((uint64_t)bin << a.coarse_shift) | (code >> 6);
+                    const unsigned shift = (code & 63u) * (unsigned)G.alpha;
+                    sat_increment(G.cells, cell, shift, G.maxc, load_cg(G.cells + cell),
+                                  &a.ctr->error);
+                }
             }
         }
         __syncthreads();
@@ -457,10 +479,12 @@ __device__ __forceinline__ void flush_totals(DevCounters *ctr, unsigned long lon
 
 template <int KW, int CHUNK, bool PART>
 __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a) {
-    __shared__ InsertSmem<KW, CHUNK, PART> S;
+    // dynamic: the partitioned variants need more than 48 KiB
+    extern __shared__ __align__(16) unsigned char insert_smem[];
+    InsertSmem<KW, CHUNK, PART> &S = *reinterpret_cast<InsertSmem<KW, CHUNK, PART> *>(insert_smem);
     const uint64_t pol_keep = policy_keep(), pol_stream = policy_stream();
     unsigned long long my_windows = 0, my_skipped = 0;
-    for (uint64_t chunk = blockIdx.x; chunk < a.nchunks; chunk += gridDim.x)
+    for (uint64_t chunk = a.chunk_begin + blockIdx.x; chunk < a.nchunks; chunk += gridDim.x)
         process_chunk<KW, CHUNK, PART>(a, chunk, S, pol_keep, pol_stream, my_windows, my_skipped);
     flush_totals(a.ctr, my_windows, my_skipped);
 }
@@ -636,23 +660,55 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
     }
 }
 
+// Exclusive prefix sum of v[0..n) into out[0..n), n <= 2 * kRepartThreads,
+// by the whole block (two entries per thread, warp shuffles, warp totals).
+__device__ __forceinline__ void repart_scan(const unsigned *v, unsigned *out, unsigned n) {
+    __shared__ unsigned warp_sum[kRepartThreads / 32];
+    const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned v0 = 2 * tid < n ? v[2 * tid] : 0u;
+    const unsigned v1 = 2 * tid + 1 < n ? v[2 * tid + 1] : 0u;
+    unsigned incl = v0 + v1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += t;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned x = lane < kRepartThreads / 32 ? warp_sum[lane] : 0u;
+        unsigned wi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= (unsigned)o) wi += t;
+        }
+        if (lane < kRepartThreads / 32) warp_sum[lane] = wi - x;
+    }
+    __syncthreads();
+    const unsigned off = warp_sum[warp] + incl - (v0 + v1);
+    if (2 * tid < n) out[2 * tid] = off;
+    if (2 * tid + 1 < n) out[2 * tid + 1] = off + v0;
+}
+
 // Split each coarse region's increment codes into slices of 2^kSliceShift
-// cells.  Block (x, y) takes tile x of coarse region y.
+// cells.  Block (x, y) takes tile x of coarse region y.  MAXF bounds the
+// slices per region (2^(coarse_shift - kSliceShift)).
+template <int MAXF>
 __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p) {
     extern __shared__ uint32_t rp_smem[];
     uint32_t *staged = rp_smem, *sorted = rp_smem + kRepartTile;
-    __shared__ unsigned hist[kCoarseBins], start[kCoarseBins], fill[kCoarseBins];
-    __shared__ unsigned long long base[kCoarseBins];
+    __shared__ unsigned hist[MAXF], start[MAXF], fill[MAXF];
+    __shared__ unsigned long long base[MAXF];
     const unsigned b = blockIdx.y, tid = threadIdx.x;
     const uint64_t n = p.coarse_written[b];
     const uint64_t t0 = (uint64_t)blockIdx.x * kRepartTile;
     if (t0 >= n) return;
     const unsigned cnt = (unsigned)min((uint64_t)kRepartTile, n - t0);
     const unsigned fpc = 1u << (p.coarse_shift - kSliceShift);   // slices per coarse region
-    const uint32_t cmask = (1u << p.coarse_shift) - 1;
-    if (tid < kCoarseBins) {
-        hist[tid] = 0;
-        fill[tid] = 0;
+    for (unsigned f = tid; f < fpc; f += kRepartThreads) {
+        hist[f] = 0;
+        fill[f] = 0;
     }
     __syncthreads();
     // 16 codes per thread, all loads issued before use (the region is 16-byte
@@ -680,38 +736,44 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
         for (int q = 0; q < 4; ++q) {
             if (i + q < cnt) {
                 staged[i + q] = c16[4 * j + q];
-                atomicAdd(&hist[((c16[4 * j + q] >> 6) & cmask) >> kSliceShift], 1u);
+                atomicAdd(&hist[c16[4 * j + q] >> (6 + kSliceShift)], 1u);
             }
         }
     }
     __syncthreads();
-    if (tid < fpc) {
-        unsigned pre = 0;
-        for (unsigned f = 0; f < tid; ++f) pre += hist[f];
-        start[tid] = pre;
-        const unsigned m = hist[tid];
+    if (MAXF <= 64) {
+        if (tid < fpc) {
+            unsigned pre = 0;
+            for (unsigned f = 0; f < tid; ++f) pre += hist[f];
+            start[tid] = pre;
+        }
+    } else {
+        repart_scan(hist, start, fpc);
+    }
+    for (unsigned f = tid; f < fpc; f += kRepartThreads) {
+        const unsigned m = hist[f];
         unsigned long long b0 = ~0ull;
         if (m) {
-            const uint64_t F = (uint64_t)b * fpc + tid;
+            const uint64_t F = (uint64_t)b * fpc + f;
             b0 = atomicAdd(p.fine_cursor + F, (unsigned long long)m);
             if (b0 + m > p.fine_cap)
                 b0 = ~0ull;
             else
                 atomicAdd(p.fine_written + F, (unsigned long long)m);
         }
-        base[tid] = b0;
+        base[f] = b0;
     }
     __syncthreads();
     for (unsigned i = tid; i < cnt; i += kRepartThreads) {
         const uint32_t code = staged[i];
-        const unsigned f = ((code >> 6) & cmask) >> kSliceShift;
+        const unsigned f = code >> (6 + kSliceShift);
         sorted[start[f] + atomicAdd(&fill[f], 1u)] = code;
     }
     __syncthreads();
     const uint32_t smask = (1u << kSliceShift) - 1;
     for (unsigned i = tid; i < cnt; i += kRepartThreads) {
         const uint32_t code = sorted[i];
-        const uint32_t word = (code >> 6) & cmask;
+        const uint32_t word = code >> 6;
         const unsigned f = word >> kSliceShift;
         const unsigned long long b0 = base[f];
         if (b0 != ~0ull) {
@@ -734,9 +796,10 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
     const uint64_t w0 = s << p.slice_shift;
     const uint64_t slice = 1ull << p.slice_shift;
     const unsigned nw = (unsigned)min(slice, p.G.words - w0);
+    const uint64_t n = p.written[s];
+    if (n == 0) return;   // no increments for this slice
     for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) cells_s[i] = p.G.cells[w0 + i];
     __syncthreads();
-    const uint64_t n = p.written[s];
     const uint32_t *src = p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
     const uint32_t wmask = (uint32_t)(slice - 1);
     const uint64_t maxc = p.G.maxc;
@@ -787,19 +850,34 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
     for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) p.G.cells[w0 + i] = cells_s[i];
 }
 
+// Launch insert_kernel<KW, CHUNK, PART> (g blocks), or with g == 0 report its
+// resident blocks per SM in *per_sm.
+template <int KW, int CHUNK, bool PART>
+cudaError_t insert_variant(const InsertArgs *a, unsigned g, cudaStream_t s, int *per_sm) {
+    const int smem = (int)sizeof(InsertSmem<KW, CHUNK, PART>);
+    cudaError_t e = cudaFuncSetAttribute(insert_kernel<KW, CHUNK, PART>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, insert_kernel<KW, CHUNK, PART>,
+                                                             kInsertThreads, smem);
+    insert_kernel<KW, CHUNK, PART><<<g, kInsertThreads, smem, s>>>(*a);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_insert(const InsertArgs *a, int kw, bool part, unsigned g, cudaStream_t s,
+                            int *per_sm) {
+    if (part && kw == 1) return insert_variant<1, kPartChunk, true>(a, g, s, per_sm);
+    if (part) return insert_variant<2, kPartChunk, true>(a, g, s, per_sm);
+    if (kw == 1) return insert_variant<1, kChunk, false>(a, g, s, per_sm);
+    return insert_variant<2, kChunk, false>(a, g, s, per_sm);
+}
+
 }  // namespace
 
 int insert_blocks_per_sm(int kw, bool partitioned) {
     int n = 0;
-    if (partitioned)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_kernel<1, kPartChunk, true>,
-                                                      kInsertThreads, 0);
-    else if (kw == 1)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_kernel<1, kChunk, false>,
-                                                      kInsertThreads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, insert_kernel<2, kChunk, false>,
-                                                      kInsertThreads, 0);
+    if (dispatch_insert(nullptr, kw, partitioned, 0, 0, &n) != cudaSuccess) n = 0;
     return n > 0 ? n : 1;
 }
 
@@ -867,11 +945,21 @@ cudaError_t launch_insert_batch(const InsertArgs *args, const unsigned long long
 cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s) {
     const uint64_t tiles = (p.coarse_cap + kRepartTile - 1) / kRepartTile;
     if (tiles == 0) return cudaSuccess;
+    if (p.coarse_shift - kSliceShift > kMaxCoarseShift - kSliceShift) return cudaErrorInvalidValue;
     const int smem = 2 * kRepartTile * (int)sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(repartition_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    repartition_kernel<<<dim3((unsigned)tiles, kCoarseBins), kRepartThreads, smem, s>>>(p);
+    const dim3 grid((unsigned)tiles, kCoarseBins);
+    cudaError_t e;
+    if (p.coarse_shift - kSliceShift <= 6) {
+        e = cudaFuncSetAttribute(repartition_kernel<64>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        repartition_kernel<64><<<grid, kRepartThreads, smem, s>>>(p);
+    } else {
+        e = cudaFuncSetAttribute(repartition_kernel<kMaxFine>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        repartition_kernel<kMaxFine><<<grid, kRepartThreads, smem, s>>>(p);
+    }
     return cudaGetLastError();
 }
 
@@ -886,15 +974,10 @@ cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
 }
 
 cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s) {
-    if (a.nchunks == 0) return cudaSuccess;
-    uint64_t g = a.nchunks < (uint64_t)grid ? a.nchunks : (uint64_t)grid;
-    if (a.part)
-        insert_kernel<1, kPartChunk, true><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
-    else if (a.K <= 32)
-        insert_kernel<1, kChunk, false><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
-    else
-        insert_kernel<2, kChunk, false><<<(unsigned)g, kInsertThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    if (a.nchunks <= a.chunk_begin) return cudaSuccess;
+    const uint64_t n = a.nchunks - a.chunk_begin;
+    const uint64_t g = n < (uint64_t)grid ? n : (uint64_t)grid;
+    return dispatch_insert(&a, a.K <= 32 ? 1 : 2, a.part != 0, (unsigned)g, s, nullptr);
 }
 
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,

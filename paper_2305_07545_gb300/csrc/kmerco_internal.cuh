@@ -16,7 +16,9 @@ constexpr int kPartChunk = 1024;           // the same in the partitioned update
 constexpr int kPartMaxHash = 4;            // hashes the partitioned design stages per window
 constexpr int kCoarseBins = 64;            // coarse countBF regions of the partitioned design
 constexpr int kSliceShift = 14;            // 2^14 cells (128 KiB) per shared-memory slice
-constexpr int kMaxCoarseShift = 20;        // cell-in-region bits of an increment code
+constexpr int kMaxCoarseShift = 24;        // cell-in-region bits of an increment code
+constexpr int kMaxFine = 1 << (kMaxCoarseShift - kSliceShift);   // slices per coarse region
+constexpr uint64_t kMaxBatchCodes = 1ull << 31;   // increments staged per partitioned pass
 constexpr int kRepartTile = 8192;          // codes per repartition block
 constexpr int kRepartThreads = 512;
 constexpr int kApplyThreads = 1024;
@@ -241,9 +243,11 @@ struct InsertArgs {
     uint64_t nreads;
     uint64_t first, last;        // offsets[0], offsets[nreads]
     const uint32_t *first_read;  // per chunk: first read starting at or after the chunk
+    uint64_t chunk_begin;        // insert_kernel takes chunks [chunk_begin, nchunks)
     uint64_t nchunks;
     int K;
-    int canonical;
+    int canonical;               // 0 forward strand, 1 lexicographic minimum, 2 smaller H_0
+    int whole_file;              // windows run across read boundaries
     Geometry G;
     uint64_t *table;             // distinct-key set, cap slots of kw words
     uint64_t cap;

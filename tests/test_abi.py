@@ -69,10 +69,11 @@ def test_python_error_type(lib):
     assert e.value.status == kc.EINVAL
 
 
-@pytest.mark.parametrize("k,m,nhash", [(33, 1 << 20, 4), (21, 1 << 20, 5), (21, 1 << 33, 4)])
+@pytest.mark.parametrize("k,m,nhash", [(33, 1 << 20, 5), (21, 1 << 20, 5), (21, 1 << 35, 4),
+                                         (55, (1 << 34) + 16, 4)])
 def test_partitioned_mode_limits(lib, k, m, nhash):
-    # the partitioned update design needs one-word keys, k_h <= 4 and at most
-    # 2^26 cells; asking for it otherwise is rejected before any GPU work
+    # the partitioned update design needs k_h <= 4 and at most 2^30 cells;
+    # asking for it otherwise is rejected before any GPU work
     with pytest.raises(kc.KmercoError) as e:
         kc.kmerco_create_ex(k, m, 4, nhash, 3, update_mode=kc.UPDATE_PARTITIONED)
     assert e.value.status == kc.EINVAL
@@ -88,8 +89,8 @@ def test_two_dimensional_geometry_limits(lib, dims):
     with pytest.raises(kc.KmercoError) as e:
         kc.kmerco_create_ex(21, 1 << 20, 4, 3, 2, dims=dims)
     assert e.value.status == kc.EINVAL
-    with pytest.raises(kc.KmercoError) as e:   # 2^26 + cells: too many for the partitioned design
-        kc.kmerco_create_ex(21, 0, 4, 3, 2, update_mode=kc.UPDATE_PARTITIONED, dims=(8209, 8219))
+    with pytest.raises(kc.KmercoError) as e:   # over 2^30 cells: too many for the partitioned design
+        kc.kmerco_create_ex(21, 0, 4, 3, 2, update_mode=kc.UPDATE_PARTITIONED, dims=(32771, 32783))
     assert e.value.status == kc.EINVAL
 
 
@@ -102,3 +103,16 @@ def test_paper_dims_entry_point_matches_the_oracle(lib):
         with pytest.raises(kc.KmercoError) as e:
             kc.kmerco_paper_dims(n, fpp)
         assert e.value.status == kc.EINVAL
+
+
+def test_variant_flags_are_checked(lib):
+    for kw in (dict(canonical_hash=True, forward_only=True),):
+        with pytest.raises(kc.KmercoError) as e:
+            kc.kmerco_create_ex(21, 1 << 12, 4, 3, 2, **kw)
+        assert e.value.status == kc.EINVAL
+    cfg = kc.kmerco_config_t(21, 1 << 12, 4, 3, 2, 0, None, 0, -1, 0, 0, 0, 0, 2, 0)
+    h = ctypes.c_void_p(1)
+    assert lib.kmerco_create_ex(ctypes.byref(cfg), ctypes.byref(h)) == kc.EINVAL   # whole_file = 2
+    cfg.whole_file, cfg.canonical_hash = 0, 3
+    assert lib.kmerco_create_ex(ctypes.byref(cfg), ctypes.byref(h)) == kc.EINVAL
+    assert h.value is None

@@ -25,9 +25,11 @@ def _dev(a: np.ndarray):
 
 
 def gpu_run(bases, offsets, K, m, alpha, nhash, tau, device_inputs=True, forward_only=False,
-            batches=None, update_mode=0, dims=None):
+            batches=None, update_mode=0, dims=None, pass_codes=0, canonical_hash=False,
+            whole_file=False):
     with kc.CountBF(K, m, alpha, nhash, tau, forward_only=forward_only,
-                    update_mode=update_mode, dims=dims) as bf:
+                    update_mode=update_mode, dims=dims, pass_codes=pass_codes,
+                    canonical_hash=canonical_hash, whole_file=whole_file) as bf:
         parts = batches or [(bases, offsets)]
         for b, o in parts:
             if device_inputs:
@@ -46,12 +48,14 @@ def _split_keys(keys, K):
     return keys[:, 1].copy(), keys[:, 0].copy()
 
 
-def check(g, bases, offsets, K, alpha, nhash, tau, forward_only=False):
+def check(g, bases, offsets, K, alpha, nhash, tau, forward_only=False, cross_check=True,
+          canonical_hash=False, whole_file=False):
     st = g["stats"]
     m = st["m_actual"]
     dims = (st["dim_x"], st["dim_y"]) if st["dim_x"] else None
     ref = oracle.run(bases, offsets, K, m, alpha, nhash, tau, canonical=not forward_only,
-                     dims=dims)
+                     dims=dims, cross_check=cross_check, canonical_hash=canonical_hash,
+                     whole_file=whole_file)
     assert np.array_equal(g["counters"], ref.filter), "countBF cells"
     hi, lo = _split_keys(g["keys"], K)
     assert np.array_equal(lo, ref.distinct_lo) and np.array_equal(hi, ref.distinct_hi), "distinct"
@@ -358,3 +362,53 @@ def test_single_sample_workload_full_size():
     assert np.array_equal(g["est"].astype(np.uint64), est)
     assert np.array_equal(g["trusted"], dlo[tr])
     assert np.array_equal(g["erroneous"], dlo[~tr])
+
+
+@pytest.mark.parametrize("K,pass_codes", [(21, 20000), (40, 50000), (55, 7777), (31, 1)])
+def test_partitioned_in_several_passes(K, pass_codes):
+    # a batch with more increments than one pass stages runs as consecutive
+    # chunk ranges, each staged, repartitioned and applied on its own
+    b, o = readsim.scaled("tiny", 4000, seed_offset=21).generate()
+    g = gpu_run(b, o, K, 1 << 22, 4, 3, 2, update_mode=kc.UPDATE_PARTITIONED,
+                pass_codes=pass_codes)
+    check(g, b, o, K, 4, 3, 2)
+    assert g["stats"]["launches"] > 20
+
+
+@pytest.mark.parametrize("K", [21, 55])
+def test_partitioned_wide_countbf(K):
+    # 2^31 4-bit counters = 2^27 cells (1 GiB): 128 slices per coarse region
+    b, o = readsim.scaled("tiny", 3000, seed_offset=22).generate()
+    g = gpu_run(b, o, K, 1 << 31, 4, 4, 2, update_mode=kc.UPDATE_PARTITIONED)
+    assert g["stats"]["words"] == 1 << 27
+    check(g, b, o, K, 4, 4, 2, cross_check=False)
+
+
+def test_partitioned_wide_two_dimensional():
+    # 8209 x 8219 cells (just over 2^26), uneven last slice
+    b, o = readsim.scaled("tiny", 2500, seed_offset=23).generate()
+    g = gpu_run(b, o, 25, 0, 8, 4, 2, update_mode=kc.UPDATE_PARTITIONED, dims=(8209, 8219),
+                pass_codes=300000)
+    check(g, b, o, 25, 8, 4, 2)
+
+
+@pytest.mark.parametrize("K", [21, 31, 32, 40, 55, 64])
+@pytest.mark.parametrize("mode", [kc.UPDATE_ATOMIC, kc.UPDATE_PARTITIONED])
+def test_hash_canonical_and_whole_file(K, mode):
+    # the paper-literal variants: canonical = strand with the smaller H_0,
+    # windows across read boundaries; each alone and both together
+    b, o = readsim.random_reads(900, 0, 160, seed=700 + K, alphabet=b"ACGTacgtN",
+                                weights=[24, 24, 24, 24, 1, 1, 1, 1, 0.3])
+    for ch, wf in ((True, False), (False, True), (True, True)):
+        g = gpu_run(b, o, K, 1 << 20, 4, 4, 2, update_mode=mode, canonical_hash=ch,
+                    whole_file=wf, device_inputs=(K % 2 == 0))
+        check(g, b, o, K, 4, 4, 2, canonical_hash=ch, whole_file=wf)
+
+
+def test_whole_file_short_reads():
+    # every read shorter than K: no window inside a read, many across them
+    b, o = readsim.random_reads(3000, 1, 15, seed=77)
+    g = gpu_run(b, o, 21, 1 << 16, 4, 3, 2, whole_file=True)
+    ref = check(g, b, o, 21, 4, 3, 2, whole_file=True)
+    assert ref.n_windows == int(o[-1]) - 21 + 1
+    assert gpu_run(b, o, 21, 1 << 16, 4, 3, 2)["stats"]["windows"] == 0
