@@ -24,7 +24,7 @@ struct kmerco {
     bool own_stream;
     int update_mode;         // 0 automatic, 1 atomic, 2 partitioned
     uint64_t pass_codes;     // increments staged per partitioned pass
-    int grid_atomic, grid_part;
+    int grid_atomic, grid_part, grid_wide;   // insert grids: atomic, partitioned, wide partitioned
     uint64_t budget, used;
     Geometry G;
     DevCounters *ctr;        // device
@@ -337,8 +337,9 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
         if (sms <= 0) sms = 1;
         h->update_mode = cfg->update_mode;
         h->pass_codes = cfg->pass_codes ? cfg->pass_codes : kMaxBatchCodes;
-        h->grid_atomic = sms * insert_blocks_per_sm(h->kw, false);
-        h->grid_part = sms * insert_blocks_per_sm(h->kw, true);
+        h->grid_atomic = sms * insert_blocks_per_sm(h->kw, 0);
+        h->grid_part = sms * insert_blocks_per_sm(h->kw, 1);
+        h->grid_wide = sms * insert_blocks_per_sm(h->kw, 2);
 
         const uint64_t eta = (uint64_t)h->eta;
         h->G = make_geometry((cfg->m + eta - 1) / eta, cfg->dim_x, cfg->dim_y, h->alpha,
@@ -475,7 +476,7 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     bool part = use_partitioned(h);
     int coarse_shift = 0, slice_shift = 0;
     uint64_t coarse_cap = 0, fine_cap = 0, nslices = 0, passes = 1;
-    bool repart = false;
+    bool repart = false, count = false;
     if (part) {
         const uint64_t W = h->G.words, U = bound * (uint64_t)h->nhash;
         const uint64_t part_chunks = (nbytes + kPartChunk - 1) / kPartChunk;
@@ -485,8 +486,16 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
         const uint64_t Up = (U + passes - 1) / passes;   // increments per pass, on average
         coarse_shift = ceil_log2(W) - 6;
         if (coarse_shift < 0) coarse_shift = 0;
-        repart = coarse_shift > kSliceShift;
-        slice_shift = repart ? kSliceShift : coarse_shift;
+        // counting apply for alpha <= 15: slices of kCountLanes / eta cells
+        // (rounded down to a power of two); compare-and-swap apply otherwise,
+        // or when the slices would be too many for one coarse region
+        int count_shift = 0;
+        while ((2ull << count_shift) * (uint64_t)h->eta <= (uint64_t)kCountLanes) ++count_shift;
+        count = h->alpha <= 15 &&
+                coarse_shift - count_shift <= kMaxCoarseShift - kSliceShift;
+        slice_shift = count ? count_shift : kSliceShift;
+        repart = coarse_shift > slice_shift;
+        if (!repart) slice_shift = coarse_shift;
         nslices = (W + (1ull << slice_shift) - 1) >> slice_shift;
         coarse_cap = Up / kCoarseBins;
         coarse_cap = (coarse_cap + coarse_cap / 6 + 4096 + 3) & ~3ull;   // multiple of 4 codes
@@ -536,7 +545,8 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
         if (part)
             KM_CUDA(cudaMemsetAsync(h->part_ctr, 0, (2 * kCoarseBins + 2 * nslices) * 8,
                                     h->stream));
-        KM_CUDA(launch_insert(a, part ? h->grid_part : h->grid_atomic, h->stream));
+        KM_CUDA(launch_insert(a, !part ? h->grid_atomic
+                                 : coarse_shift <= 20 ? h->grid_part : h->grid_wide, h->stream));
         h->launches += a.nchunks > a.chunk_begin ? 1 : 0;
         if (!part) continue;
         unsigned long long *fine_cursor = h->part_ctr + 2 * kCoarseBins;
@@ -545,6 +555,7 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
             PartArgs p;
             p.G = h->G;
             p.coarse_shift = coarse_shift;
+            p.slice_shift = slice_shift;
             p.coarse = h->coarse;
             p.coarse_cap = coarse_cap;
             p.coarse_written = a.coarse_written;
@@ -563,7 +574,8 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
         ap.cap = repart ? fine_cap : coarse_cap;
         ap.written = repart ? fine_written : a.coarse_written;
         ap.ctr = h->ctr;
-        KM_CUDA(launch_apply(ap, nslices, h->stream));
+        KM_CUDA(count ? launch_apply_count(ap, nslices, h->stream)
+                      : launch_apply(ap, nslices, h->stream));
         h->launches += 1;
     }
     KM_CUDA(cudaEventRecord(h->ev[1], h->stream));

@@ -4,7 +4,7 @@
 //  - radix_sort: least-significant-digit radix sort of the distinct keys
 //    (8-bit digits, only the 2K bits a key can use).  Per pass: per-tile
 //    digit counts, one scan per digit across tiles, then a stable scatter
-//    in which each warp ranks equal digits with __match_any_sync and the
+//    in which each warp ranks equal digits with one ballot per digit bit and the
 //    tile is reordered in shared memory before coalesced stores.
 //  - bucket_sort (one-word keys): the top 12 of the 2K key bits split the
 //    keys into 4096 buckets in one scatter pass (cursor atomics aggregated
@@ -169,7 +169,14 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint64_t 
     const unsigned lt = (1u << lane) - 1;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[j]);
+        // lanes holding the same digit: one ballot per digit bit
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < kRadixBits; ++b) {
+            const bool bit = (dig[j] >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
         const unsigned prev = wcnt[warp][dig[j]];
         __syncwarp();
         if (lane == __ffs(peers) - 1) wcnt[warp][dig[j]] = prev + __popc(peers);

@@ -42,7 +42,7 @@ struct ChunkDims {
     static constexpr int kRaw = kPack32 * 16 + 32;   // >= CHUNK + 63 bases + alignment slack
 };
 
-template <int KW, int CHUNK, bool PART>
+template <int KW, int CHUNK, int PART>
 struct __align__(16) InsertSmem {
     uint8_t raw[ChunkDims<CHUNK>::kRaw];        // raw[head + q] = base q of the chunk
     uint32_t pk[ChunkDims<CHUNK>::kPack32];     // codes; word t at t ^ 1 so pairs read as u64
@@ -53,7 +53,7 @@ struct __align__(16) InsertSmem {
     // partitioned design: the chunk's counter-increment codes
     uint32_t staged[PART ? CHUNK * kPartMaxHash : 1];
     uint32_t sorted[PART ? CHUNK * kPartMaxHash : 1];
-    uint8_t sbin[PART ? CHUNK * kPartMaxHash : 1];   // coarse region of staged[i]
+    uint8_t sbin[PART == 2 ? CHUNK * kPartMaxHash : 1];   // coarse region of staged[i]
     unsigned hist[PART ? kCoarseBins : 1];
     unsigned start[PART ? kCoarseBins : 1];
     unsigned fill[PART ? kCoarseBins : 1];
@@ -165,7 +165,7 @@ __device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64
 
 // One chunk of CHUNK window starts (steps 1-5 above) for the sample
 // described by `a`; counts its windows into my_windows / my_skipped.
-template <int KW, int CHUNK, bool PART>
+template <int KW, int CHUNK, int PART>
 __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chunk,
                                               InsertSmem<KW, CHUNK, PART> &S, uint64_t pol_keep,
                                               uint64_t pol_stream,
@@ -195,7 +195,16 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
                 if (b >= head && b < head + nb) S.raw[b] = *(const uint8_t *)(abase + b);
         }
     }
-    for (int i = tid; i < kPack32 / 2; i += kInsertThreads) S.brk[i] = 0;
+    // read starts inside the staged span (none when the reads are one
+    // sequence), loaded alongside the bytes; S.brk is zero on entry
+    for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; !a.whole_file && r < a.nreads;
+         r += kInsertThreads) {
+        uint64_t s = a.offsets[r] - a.first;
+        if (s >= c0 + nb) break;
+        if (s < c0) continue;   // only with decreasing offsets, which the host rejects
+        unsigned q = (unsigned)(s - c0);
+        if (q > 0) atomicOr(&S.brk[q >> 5], 1u << (q & 31));
+    }
     if (tid == 0) {
         S.nvalid = 0;
         S.nfresh = 0;
@@ -223,16 +232,6 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
         S.pk[t ^ 1] = code;
         S.inv[t] = (uint16_t)bad;
     }
-    // 2b. read starts inside the staged span (none when the reads are one
-    //     sequence)
-    for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; !a.whole_file && r < a.nreads;
-         r += kInsertThreads) {
-        uint64_t s = a.offsets[r] - a.first;
-        if (s >= c0 + nb) break;
-        if (s < c0) continue;   // only with decreasing offsets, which the host rejects
-        unsigned q = (unsigned)(s - c0);
-        if (q > 0) atomicOr(&S.brk[q >> 5], 1u << (q & 31));
-    }
     __syncthreads();
 
     // 3. window starts: inside one read, K valid bases
@@ -255,6 +254,7 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
     __syncthreads();
 
     // 4. per valid window: canonical key, hashes, counter updates, set insert
+    for (int i = tid; i < kPack32 / 2; i += kInsertThreads) S.brk[i] = 0;   // for the next chunk
     const unsigned nvalid = S.nvalid;
     const uint64_t *pk64 = (const uint64_t *)S.pk;
     for (unsigned i0 = (unsigned)warp * 32; i0 < nvalid; i0 += kInsertThreads) {
@@ -354,9 +354,14 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
                     if (use[j]) {
                         const unsigned bin = (unsigned)(cell[j] >> a.coarse_shift);
                         const unsigned at = base + __popc(bal & ((1u << lane) - 1));
-                        S.staged[at] =
+                        const uint32_t code =
                             ((uint32_t)(cell[j] & ((1ull << a.coarse_shift) - 1)) << 6) | slot[j];
-                        S.sbin[at] = (uint8_t)bin;
+                        if (PART == 2) {   // region beside the code
+                            S.staged[at] = code;
+                            S.sbin[at] = (uint8_t)bin;
+                        } else {           // region in the top 6 bits (coarse_shift <= 20)
+                            S.staged[at] = (bin << 26) | code;
+                        }
                         atomicAdd(&S.hist[bin], 1u);
                     }
                 }
@@ -396,15 +401,34 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
     }
     __syncthreads();
 
+    // 4b. reservations, all in one phase: the distinct-list run of this
+    //     chunk's new keys, and (partitioned design) one cursor atomic per
+    //     coarse region for the chunk's increment codes
+    const unsigned nfresh = S.nfresh;
+    if (tid == kCoarseBins && nfresh) {
+        unsigned long long b = atomicAdd(&a.ctr->distinct, (unsigned long long)nfresh);
+        if (b + nfresh > a.dlist_cap) {
+            atomicOr(&a.ctr->error, kErrListFull);
+            b = ~0ull;
+        }
+        S.fresh_base = b;
+    }
     if (PART) {
-        // 4b. counting sort of the increment codes by coarse region, one
-        //     cursor atomic per region, coalesced runs into the regions
         const unsigned nupd = S.nupd;
-        if (tid < kCoarseBins) {
-            unsigned pre = 0;
-            for (int b = 0; b < tid; ++b) pre += S.hist[b];
-            S.start[tid] = pre;
+        if (tid < kCoarseBins) {   // warps 0 and 1: prefix over the regions
             const unsigned n = S.hist[tid];
+            unsigned incl = n, below = 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (unsigned)o) incl += t;
+            }
+            if (tid >= 32) {   // warp 1 starts after all of warp 0's regions
+                below = S.hist[tid - 32];
+#pragma unroll
+                for (int o = 16; o; o >>= 1) below += __shfl_xor_sync(0xffffffffu, below, o);
+            }
+            S.start[tid] = below + incl - n;
             unsigned long long b0 = ~0ull;
             if (n) {
                 b0 = atomicAdd(a.coarse_cursor + tid, (unsigned long long)n);
@@ -416,12 +440,19 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
             S.base[tid] = b0;
         }
         __syncthreads();
+        // 4c. counting sort of the codes by coarse region in shared memory
         for (unsigned i = tid; i < nupd; i += kInsertThreads) {
-            const unsigned bin = S.sbin[i];
-            S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = S.staged[i];
+            if (PART == 2) {
+                const unsigned bin = S.sbin[i];
+                S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = S.staged[i];
+            } else {
+                const uint32_t c = S.staged[i];
+                const unsigned bin = c >> 26;
+                S.sorted[S.start[bin] + atomicAdd(&S.fill[bin], 1u)] = c & 0x3FFFFFFu;
+            }
         }
         __syncthreads();
-        // one warp per region run: contiguous stores into the region
+        // 4d. one warp per region run: contiguous stores into the region
         for (unsigned bin = warp; bin < kCoarseBins; bin += kInsertThreads / 32) {
             const unsigned n = S.hist[bin], s0 = S.start[bin];
             const unsigned long long b0 = S.base[bin];
@@ -438,21 +469,12 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
                 }
             }
         }
+    } else {
         __syncthreads();
     }
 
-    // 5. append this chunk's new keys to the distinct list
-    const unsigned nfresh = S.nfresh;
+    // 5. this chunk's new keys into the distinct list
     if (nfresh) {
-        if (tid == 0) {
-            unsigned long long b = atomicAdd(&a.ctr->distinct, (unsigned long long)nfresh);
-            if (b + nfresh > a.dlist_cap) {
-                atomicOr(&a.ctr->error, kErrListFull);
-                b = ~0ull;
-            }
-            S.fresh_base = b;
-        }
-        __syncthreads();
         const unsigned long long b = S.fresh_base;
         if (b != ~0ull)
             for (unsigned i = tid; i < nfresh * KW; i += kInsertThreads)
@@ -477,11 +499,13 @@ __device__ __forceinline__ void flush_totals(DevCounters *ctr, unsigned long lon
     k = 0;
 }
 
-template <int KW, int CHUNK, bool PART>
+template <int KW, int CHUNK, int PART>
 __global__ void __launch_bounds__(kInsertThreads, 4) insert_kernel(InsertArgs a) {
     // dynamic: the partitioned variants need more than 48 KiB
     extern __shared__ __align__(16) unsigned char insert_smem[];
     InsertSmem<KW, CHUNK, PART> &S = *reinterpret_cast<InsertSmem<KW, CHUNK, PART> *>(insert_smem);
+    for (int i = threadIdx.x; i < ChunkDims<CHUNK>::kPack32 / 2; i += kInsertThreads) S.brk[i] = 0;
+    __syncthreads();
     const uint64_t pol_keep = policy_keep(), pol_stream = policy_stream();
     unsigned long long my_windows = 0, my_skipped = 0;
     for (uint64_t chunk = a.chunk_begin + blockIdx.x; chunk < a.nchunks; chunk += gridDim.x)
@@ -498,10 +522,11 @@ template <int KW, int CHUNK>
 __global__ void __launch_bounds__(kInsertThreads, 4) insert_batch_kernel(
     const InsertArgs *args, const unsigned long long *chunk_end, int nsamples,
     unsigned long long total_chunks) {
-    __shared__ InsertSmem<KW, CHUNK, false> S;
+    __shared__ InsertSmem<KW, CHUNK, 0> S;
     __shared__ InsertArgs A;
     const uint64_t pol_keep = policy_keep(), pol_stream = policy_stream();
     unsigned long long my_windows = 0, my_skipped = 0;
+    for (int i = threadIdx.x; i < ChunkDims<CHUNK>::kPack32 / 2; i += kInsertThreads) S.brk[i] = 0;
     int s = -1;
     unsigned long long s_begin = 0;
     for (unsigned long long chunk = blockIdx.x; chunk < total_chunks; chunk += gridDim.x) {
@@ -515,7 +540,7 @@ __global__ void __launch_bounds__(kInsertThreads, 4) insert_batch_kernel(
             s_begin = t ? chunk_end[t - 1] : 0;
             __syncthreads();
         }
-        process_chunk<KW, CHUNK, false>(A, chunk - s_begin, S, pol_keep, pol_stream, my_windows,
+        process_chunk<KW, CHUNK, 0>(A, chunk - s_begin, S, pol_keep, pol_stream, my_windows,
                                         my_skipped);
     }
     if (s >= 0) flush_totals(A.ctr, my_windows, my_skipped);
@@ -705,7 +730,8 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
     const uint64_t t0 = (uint64_t)blockIdx.x * kRepartTile;
     if (t0 >= n) return;
     const unsigned cnt = (unsigned)min((uint64_t)kRepartTile, n - t0);
-    const unsigned fpc = 1u << (p.coarse_shift - kSliceShift);   // slices per coarse region
+    const int fsh = 6 + p.slice_shift;                            // code >> fsh = slice
+    const unsigned fpc = 1u << (p.coarse_shift - p.slice_shift);  // slices per coarse region
     for (unsigned f = tid; f < fpc; f += kRepartThreads) {
         hist[f] = 0;
         fill[f] = 0;
@@ -736,7 +762,7 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
         for (int q = 0; q < 4; ++q) {
             if (i + q < cnt) {
                 staged[i + q] = c16[4 * j + q];
-                atomicAdd(&hist[c16[4 * j + q] >> (6 + kSliceShift)], 1u);
+                atomicAdd(&hist[c16[4 * j + q] >> fsh], 1u);
             }
         }
     }
@@ -766,15 +792,15 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
     __syncthreads();
     for (unsigned i = tid; i < cnt; i += kRepartThreads) {
         const uint32_t code = staged[i];
-        const unsigned f = code >> (6 + kSliceShift);
+        const unsigned f = code >> fsh;
         sorted[start[f] + atomicAdd(&fill[f], 1u)] = code;
     }
     __syncthreads();
-    const uint32_t smask = (1u << kSliceShift) - 1;
+    const uint32_t smask = (1u << p.slice_shift) - 1;
     for (unsigned i = tid; i < cnt; i += kRepartThreads) {
         const uint32_t code = sorted[i];
         const uint32_t word = code >> 6;
-        const unsigned f = word >> kSliceShift;
+        const unsigned f = word >> p.slice_shift;
         const unsigned long long b0 = base[f];
         if (b0 != ~0ull) {
             const uint64_t F = (uint64_t)b * fpc + f;
@@ -850,9 +876,80 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
     for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) p.G.cells[w0 + i] = cells_s[i];
 }
 
+// Counting apply (alpha <= 15): one slice of 2^slice_shift cells per block.
+// The slice's increments are counted in 16-bit shared-memory lanes, counter
+// (cell, l) at lane l * 2^slice_shift + cell; each lane stops counting at
+// 2^alpha - 1, where the counter saturates whatever its old value.  A count
+// is checked before it is incremented, so concurrent increments can carry
+// it past that bound by at most the increments in flight in the block
+// (kApplyThreads * 8), which stays below 2^16 for alpha <= 15.  Then every
+// counter becomes min(old + count, 2^alpha - 1) and the slice is written back.
+__global__ void __launch_bounds__(kApplyThreads, 1) apply_count_kernel(ApplyArgs p) {
+    extern __shared__ uint32_t lanes[];   // two 16-bit counts per word
+    const uint64_t s = blockIdx.x;
+    const uint64_t n = p.written[s];
+    if (n == 0) return;   // no increments for this slice
+    const int ssh = p.slice_shift;
+    const uint64_t w0 = s << ssh;
+    const uint64_t slice = 1ull << ssh;
+    const unsigned nw = (unsigned)min(slice, p.G.words - w0);
+    const unsigned eta = (unsigned)p.G.eta;
+    const unsigned nwords = (eta << ssh) >> 1;
+    for (unsigned i = threadIdx.x; i < nwords; i += kApplyThreads) lanes[i] = 0;
+    __syncthreads();
+    const uint32_t *src = p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
+    const uint32_t wmask = (uint32_t)(slice - 1);
+    const unsigned cap = (unsigned)p.G.maxc;
+    constexpr unsigned kStep = kApplyThreads * 8;
+    for (uint64_t i0 = 0; i0 < n; i0 += kStep) {
+        uint32_t code[8];
+        unsigned valid = 0;
+        const uint64_t i = i0 + threadIdx.x * 4ull;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t j = i + (uint64_t)h * kApplyThreads * 4;
+            if (j + 4 <= n) {
+                const uint4 v = __ldcs((const uint4 *)(src + j));
+                code[4 * h] = v.x;
+                code[4 * h + 1] = v.y;
+                code[4 * h + 2] = v.z;
+                code[4 * h + 3] = v.w;
+                valid |= 0xFu << (4 * h);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    code[4 * h + q] = j + q < n ? src[j + q] : 0u;
+                    valid |= (j + q < n ? 1u : 0u) << (4 * h + q);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (!((valid >> q) & 1u)) continue;   // past the end
+            const unsigned c = ((code[q] & 63u) << ssh) | ((code[q] >> 6) & wmask);
+            uint32_t *wp = lanes + (c >> 1);
+            const unsigned sh = (c & 1u) << 4;
+            if (((*(volatile uint32_t *)wp >> sh) & 0xFFFFu) < cap) atomicAdd(wp, 1u << sh);
+        }
+    }
+    __syncthreads();
+    const uint16_t *cnt16 = (const uint16_t *)lanes;
+    const unsigned alpha = (unsigned)p.G.alpha;
+    const uint64_t maxc = p.G.maxc;
+    for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) {
+        const uint64_t old = p.G.cells[w0 + i];
+        uint64_t out = 0;
+        for (unsigned l = 0; l < eta; ++l) {
+            const uint64_t v = ((old >> (l * alpha)) & maxc) + cnt16[((uint64_t)l << ssh) | i];
+            out |= (v < maxc ? v : maxc) << (l * alpha);
+        }
+        p.G.cells[w0 + i] = out;
+    }
+}
+
 // Launch insert_kernel<KW, CHUNK, PART> (g blocks), or with g == 0 report its
 // resident blocks per SM in *per_sm.
-template <int KW, int CHUNK, bool PART>
+template <int KW, int CHUNK, int PART>
 cudaError_t insert_variant(const InsertArgs *a, unsigned g, cudaStream_t s, int *per_sm) {
     const int smem = (int)sizeof(InsertSmem<KW, CHUNK, PART>);
     cudaError_t e = cudaFuncSetAttribute(insert_kernel<KW, CHUNK, PART>,
@@ -865,19 +962,23 @@ cudaError_t insert_variant(const InsertArgs *a, unsigned g, cudaStream_t s, int 
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_insert(const InsertArgs *a, int kw, bool part, unsigned g, cudaStream_t s,
+// part: 0 atomic design; 1 partitioned, region bits inside the codes
+// (coarse_shift <= 20); 2 partitioned, regions beside the codes.
+cudaError_t dispatch_insert(const InsertArgs *a, int kw, int part, unsigned g, cudaStream_t s,
                             int *per_sm) {
-    if (part && kw == 1) return insert_variant<1, kPartChunk, true>(a, g, s, per_sm);
-    if (part) return insert_variant<2, kPartChunk, true>(a, g, s, per_sm);
-    if (kw == 1) return insert_variant<1, kChunk, false>(a, g, s, per_sm);
-    return insert_variant<2, kChunk, false>(a, g, s, per_sm);
+    if (part == 1 && kw == 1) return insert_variant<1, kPartChunk, 1>(a, g, s, per_sm);
+    if (part == 1) return insert_variant<2, kPartChunk, 1>(a, g, s, per_sm);
+    if (part == 2 && kw == 1) return insert_variant<1, kPartChunk, 2>(a, g, s, per_sm);
+    if (part == 2) return insert_variant<2, kPartChunk, 2>(a, g, s, per_sm);
+    if (kw == 1) return insert_variant<1, kChunk, 0>(a, g, s, per_sm);
+    return insert_variant<2, kChunk, 0>(a, g, s, per_sm);
 }
 
 }  // namespace
 
-int insert_blocks_per_sm(int kw, bool partitioned) {
+int insert_blocks_per_sm(int kw, int part) {
     int n = 0;
-    if (dispatch_insert(nullptr, kw, partitioned, 0, 0, &n) != cudaSuccess) n = 0;
+    if (dispatch_insert(nullptr, kw, part, 0, 0, &n) != cudaSuccess) n = 0;
     return n > 0 ? n : 1;
 }
 
@@ -945,11 +1046,13 @@ cudaError_t launch_insert_batch(const InsertArgs *args, const unsigned long long
 cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s) {
     const uint64_t tiles = (p.coarse_cap + kRepartTile - 1) / kRepartTile;
     if (tiles == 0) return cudaSuccess;
-    if (p.coarse_shift - kSliceShift > kMaxCoarseShift - kSliceShift) return cudaErrorInvalidValue;
+    if (p.coarse_shift - p.slice_shift > kMaxCoarseShift - kSliceShift ||
+        p.coarse_shift <= p.slice_shift)
+        return cudaErrorInvalidValue;
     const int smem = 2 * kRepartTile * (int)sizeof(uint32_t);
     const dim3 grid((unsigned)tiles, kCoarseBins);
     cudaError_t e;
-    if (p.coarse_shift - kSliceShift <= 6) {
+    if (p.coarse_shift - p.slice_shift <= 6) {
         e = cudaFuncSetAttribute(repartition_kernel<64>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -973,11 +1076,24 @@ cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
+    if (nslices == 0) return cudaSuccess;
+    const size_t smem = ((size_t)p.G.eta << p.slice_shift) * 2;
+    if (smem > (size_t)kCountLanes * 2 || p.G.alpha > 15) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(apply_count_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kCountLanes * 2);
+    if (e != cudaSuccess) return e;
+    apply_count_kernel<<<(unsigned)nslices, kApplyThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s) {
     if (a.nchunks <= a.chunk_begin) return cudaSuccess;
     const uint64_t n = a.nchunks - a.chunk_begin;
     const uint64_t g = n < (uint64_t)grid ? n : (uint64_t)grid;
-    return dispatch_insert(&a, a.K <= 32 ? 1 : 2, a.part != 0, (unsigned)g, s, nullptr);
+    const int part = !a.part ? 0 : a.coarse_shift <= 20 ? 1 : 2;
+    return dispatch_insert(&a, a.K <= 32 ? 1 : 2, part, (unsigned)g, s, nullptr);
 }
 
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,

@@ -266,6 +266,7 @@ struct InsertArgs {
 struct PartArgs {
     Geometry G;
     int coarse_shift;
+    int slice_shift;                       // fine slice = cell >> slice_shift
     const uint32_t *coarse;
     uint64_t coarse_cap;
     const unsigned long long *coarse_written;
@@ -291,7 +292,9 @@ cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t
                               uint64_t nchunks, uint64_t chunk, uint32_t *first_read,
                               cudaStream_t s);
 cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s);
-int insert_blocks_per_sm(int kw, bool partitioned);
+// Resident insert blocks per SM; part: 0 atomic design, 1 partitioned with
+// region bits inside the codes (coarse_shift <= 20), 2 partitioned (wide).
+int insert_blocks_per_sm(int kw, int part);
 cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s);
 
 // Batched insertion (atomic design): many samples, each with its own
@@ -306,6 +309,11 @@ cudaError_t launch_insert_batch(const InsertArgs *args, const unsigned long long
                                 int nsamples, unsigned long long total_chunks, int kw, int chunk,
                                 int grid, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
+// Counting apply (alpha <= 15): the slice's increments are first counted in
+// 16-bit shared-memory lanes (2^slice_shift * eta of them, at most 65536),
+// then added to the counters with saturation.
+constexpr int kCountLanes = 65536;
+cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
 // Insert n keys into a distinct set; when dlist is not null, keys new to the
 // set are appended to it (ctr->distinct counts them).
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,
