@@ -267,11 +267,18 @@ int kmerco_classify_noalloc(const uint64_t *cells, uint64_t m, int k, int counte
 int kmerco_reset(kmerco_t *h);
 
 /*
- * Batches: many samples, each with its own handle and countBF, inserted by
- * one persistent kernel launch (the same per-window work as kmerco_insert,
- * atomic update design).  The handles must share device, stream, K and the
- * key width; their m, counter_bits and nhash may differ.  The paper counts
- * one sample at a time; batching is a GPU schedule, not a change of method.
+ * Batches: many samples, each with its own handle and countBF, inserted
+ * together under one CUDA graph.  Two schedules, chosen by a timed
+ * autotuner on the first input:
+ *   persistent   one kernel launch over the chunks of all samples (atomic
+ *                update design), chunk size and resident blocks tuned;
+ *   per-sample   each sample's own insert kernels (the partitioned design
+ *                where kmerco_insert would use it), samples spread over 1,
+ *                2, 4 or 8 concurrent streams, largest first.
+ * The per-window work is that of kmerco_insert either way, and so are the
+ * results.  The handles must share device, stream, K and the key width;
+ * their m, counter_bits and nhash may differ.  The paper counts one sample
+ * at a time; batching is a GPU schedule, not a change of method.
  */
 typedef struct kmerco_batch kmerco_batch_t;
 
@@ -284,6 +291,8 @@ typedef struct {
     int graph;            /* 1 when a CUDA graph of reset + insert is captured */
     uint64_t launches;    /* kernels launched by the batch */
     uint64_t total_chunks;
+    int schedule;         /* 0 persistent launch, 1 per-sample kernels on concurrent streams */
+    int streams;          /* streams of the per-sample schedule (0 for the persistent one) */
 } kmerco_batch_info_t;
 
 /* Group n handles (not owned; they must outlive the batch).  EINVAL when
@@ -297,14 +306,23 @@ void kmerco_batch_destroy(kmerco_batch_t *b);
  * Insert sample i's reads (device pointers bases[i], offsets[i], nreads[i],
  * the CSR layout of kmerco_insert) into handle i, all in one launch.  With
  * reset != 0 every handle is first reset (kmerco_reset).  The first reset
- * call times every candidate schedule (chunk 1024/2048 x resident blocks)
- * on this input, keeps the fastest, and captures reset + insert in a CUDA
- * graph; a later call with the same pointers and read counts replays it.
+ * call times every candidate schedule (persistent: chunk 1024/2048 x
+ * resident blocks; per-sample: 1, 2, 4, 8 streams) on this input, keeps the
+ * fastest, and captures reset + insert in a CUDA graph; a later call with
+ * the same pointers and read counts replays it.  The per-sample schedule
+ * holds increment-code scratch per stream for the largest sample.
  * Asynchronous except for the planning of a new input (one readback).
  * Errors: EINVAL (host pointers, decreasing offsets, mixed K); ENOMEM; ECUDA.
  */
 int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
                         const uint64_t *const *offsets, const uint64_t *nreads, int reset);
+
+/* Pin the schedule instead of tuning it: schedule 0 persistent launch (chunk
+ * 2048, 4 resident blocks per SM or fewer), 1 per-sample kernels on
+ * `streams` streams (1, 2, 4 or 8); -1 tunes again on the next reset call.
+ * The per-sample schedule falls back to the persistent one when its scratch
+ * cannot be allocated.  Errors: EINVAL. */
+int kmerco_batch_schedule(kmerco_batch_t *b, int schedule, int streams);
 
 /* kmerco_classify() of every handle of the batch, in order. */
 int kmerco_batch_classify(kmerco_batch_t *b);

@@ -48,7 +48,7 @@ class kmerco_stats_t(ctypes.Structure):
 class kmerco_batch_info_t(ctypes.Structure):
     _fields_ = [("samples", c_int), ("chunk", c_int), ("blocks_per_sm", c_int), ("tuned", c_int),
                 ("tuned_ms", c_float), ("graph", c_int), ("launches", c_uint64),
-                ("total_chunks", c_uint64)]
+                ("total_chunks", c_uint64), ("schedule", c_int), ("streams", c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -87,6 +87,7 @@ SIGNATURES = {
     "kmerco_batch_destroy": (None, [c_void_p]),
     "kmerco_batch_insert": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), _u64p, c_int]),
     "kmerco_batch_classify": (c_int, [c_void_p]),
+    "kmerco_batch_schedule": (c_int, [c_void_p, c_int, c_int]),
     "kmerco_batch_info": (c_int, [c_void_p, c_void_p]),
 }
 
@@ -263,6 +264,10 @@ def kmerco_batch_classify(b: int) -> None:
     _check(load().kmerco_batch_classify(b), "kmerco_batch_classify")
 
 
+def kmerco_batch_schedule(b: int, schedule: int, streams: int = 0) -> None:
+    _check(load().kmerco_batch_schedule(b, schedule, streams), "kmerco_batch_schedule")
+
+
 def kmerco_batch_info(b: int) -> dict:
     info = kmerco_batch_info_t()
     _check(load().kmerco_batch_info(b, byref(info)), "kmerco_batch_info")
@@ -359,7 +364,8 @@ class CountBF:
 
 
 class Batch:
-    """Several CountBF handles inserted by one persistent launch."""
+    """Several CountBF handles inserted together (persistent launch or
+    per-sample kernels on concurrent streams, as tuned or pinned)."""
 
     def __init__(self, filters: list[CountBF]):
         self.filters = list(filters)
@@ -381,6 +387,9 @@ class Batch:
 
     def classify(self) -> None:
         kmerco_batch_classify(self.b)
+
+    def schedule(self, schedule: int, streams: int = 0) -> None:
+        kmerco_batch_schedule(self.b, schedule, streams)
 
     def info(self) -> dict:
         return kmerco_batch_info(self.b)

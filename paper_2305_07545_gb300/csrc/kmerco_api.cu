@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -248,6 +249,135 @@ int ceil_log2(uint64_t x) {
     return l;
 }
 
+// ------------------------------------------------------------ insert plan
+
+// How one insert call applies its counter increments (partitioned design),
+// decided on the host from the call's window bound and input size.
+struct PartPlan {
+    bool part = false, repart = false, count = false;
+    int coarse_shift = 0, slice_shift = 0;
+    uint64_t coarse_cap = 0, fine_cap = 0, nslices = 0, passes = 1;
+    uint64_t coarse_words() const { return kCoarseBins * coarse_cap; }   // uint32 codes
+    uint64_t fine_words() const { return repart ? nslices * fine_cap : 0; }
+    uint64_t ctr_words() const { return 2 * kCoarseBins + 2 * nslices; }
+};
+
+struct PartBufs {
+    uint32_t *coarse, *fine;
+    unsigned long long *ctr;
+};
+
+// Increment-code buffers sized for one pass of at most pass_codes
+// increments; larger inputs run in several passes over consecutive chunk
+// ranges.  Counting apply for alpha <= 15 (slices of kCountLanes / eta cells,
+// rounded down to a power of two), compare-and-swap apply otherwise or when
+// the slices would be too many for one coarse region.
+PartPlan plan_partition(const kmerco_t *h, uint64_t bound, uint64_t nbytes) {
+    PartPlan pp;
+    if (!use_partitioned(h) || bound == 0) return pp;
+    pp.part = true;
+    const uint64_t W = h->G.words, U = bound * (uint64_t)h->nhash;
+    const uint64_t part_chunks = (nbytes + kPartChunk - 1) / kPartChunk;
+    pp.passes = (U + h->pass_codes - 1) / h->pass_codes;
+    if (pp.passes > part_chunks) pp.passes = part_chunks;   // a pass takes one chunk at least
+    if (pp.passes < 1) pp.passes = 1;
+    const uint64_t Up = (U + pp.passes - 1) / pp.passes;   // increments per pass, on average
+    pp.coarse_shift = ceil_log2(W) - 6;
+    if (pp.coarse_shift < 0) pp.coarse_shift = 0;
+    int count_shift = 0;
+    while ((2ull << count_shift) * (uint64_t)h->eta <= (uint64_t)kCountLanes) ++count_shift;
+    pp.count = h->alpha <= 15 && pp.coarse_shift - count_shift <= kMaxCoarseShift - kSliceShift;
+    pp.slice_shift = pp.count ? count_shift : kSliceShift;
+    pp.repart = pp.coarse_shift > pp.slice_shift;
+    if (!pp.repart) pp.slice_shift = pp.coarse_shift;
+    pp.nslices = (W + (1ull << pp.slice_shift) - 1) >> pp.slice_shift;
+    pp.coarse_cap = Up / kCoarseBins;
+    pp.coarse_cap = (pp.coarse_cap + pp.coarse_cap / 6 + 4096 + 3) & ~3ull;   // multiple of 4
+    pp.fine_cap = pp.repart ? Up / pp.nslices : 0;
+    pp.fine_cap = (pp.fine_cap + pp.fine_cap / 5 + 1024 + 3) & ~3ull;
+    return pp;
+}
+
+// Insert arguments of one call that do not depend on the plan.
+InsertArgs sample_args(const kmerco_t *h, const uint8_t *d_bases, const uint64_t *d_off,
+                       uint64_t nreads, uint64_t first, uint64_t last) {
+    InsertArgs a;
+    memset(&a, 0, sizeof(a));
+    a.bases = d_bases;
+    a.offsets = d_off;
+    a.nreads = nreads;
+    a.first = first;
+    a.last = last;
+    a.first_read = h->first_read;
+    a.K = h->K;
+    a.canonical = h->canonical;
+    a.whole_file = h->whole_file;
+    a.G = h->G;
+    a.table = h->table;
+    a.cap = h->cap;
+    a.dlist = h->dlist;
+    a.dlist_cap = h->dlist_cap;
+    a.ctr = h->ctr;
+    return a;
+}
+
+// All device work of one insert call on stream s, without host
+// synchronisation (so it can be captured): first reads of the chunks, then
+// per pass the insert kernel and, in the partitioned design, repartition and
+// apply.  h->first_read must hold the call's chunks; pb holds pp's buffers.
+int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
+                         const PartBufs &pb, cudaStream_t s, uint64_t &launches) {
+    const uint64_t nbytes = a.last - a.first;
+    const uint64_t chunk = pp.part ? kPartChunk : kChunk;
+    const uint64_t nchunks = (nbytes + chunk - 1) / chunk;
+    KM_CUDA(launch_first_read(a.offsets, a.nreads, a.first, nchunks, chunk, h->first_read, s));
+    launches += nchunks ? 1 : 0;
+    a.part = pp.part ? 1 : 0;
+    a.coarse_shift = pp.coarse_shift;
+    a.coarse = pb.coarse;
+    a.coarse_cap = pp.coarse_cap;
+    a.coarse_cursor = pb.ctr;
+    a.coarse_written = pb.ctr ? pb.ctr + kCoarseBins : nullptr;
+    const int grid = !pp.part ? h->grid_atomic : pp.coarse_shift <= 20 ? h->grid_part
+                                                                       : h->grid_wide;
+    for (uint64_t pass = 0; pass < pp.passes; ++pass) {
+        a.chunk_begin = nchunks * pass / pp.passes;
+        a.nchunks = nchunks * (pass + 1) / pp.passes;
+        if (pp.part) KM_CUDA(cudaMemsetAsync(pb.ctr, 0, pp.ctr_words() * 8, s));
+        KM_CUDA(launch_insert(a, grid, s));
+        launches += a.nchunks > a.chunk_begin ? 1 : 0;
+        if (!pp.part) continue;
+        unsigned long long *fine_cursor = pb.ctr + 2 * kCoarseBins;
+        unsigned long long *fine_written = fine_cursor + pp.nslices;
+        if (pp.repart) {
+            PartArgs p;
+            p.G = h->G;
+            p.coarse_shift = pp.coarse_shift;
+            p.slice_shift = pp.slice_shift;
+            p.coarse = pb.coarse;
+            p.coarse_cap = pp.coarse_cap;
+            p.coarse_written = a.coarse_written;
+            p.fine = pb.fine;
+            p.fine_cap = pp.fine_cap;
+            p.fine_cursor = fine_cursor;
+            p.fine_written = fine_written;
+            p.ctr = h->ctr;
+            KM_CUDA(launch_repartition(p, s));
+            launches += 1;
+        }
+        ApplyArgs ap;
+        ap.G = h->G;
+        ap.slice_shift = pp.slice_shift;
+        ap.codes = pp.repart ? pb.fine : pb.coarse;
+        ap.cap = pp.repart ? pp.fine_cap : pp.coarse_cap;
+        ap.written = pp.repart ? fine_written : a.coarse_written;
+        ap.ctr = h->ctr;
+        KM_CUDA(pp.count ? launch_apply_count(ap, pp.nslices, s) : launch_apply(ap, pp.nslices, s));
+        launches += 1;
+    }
+    return KMERCO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -426,31 +556,22 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     DeviceGuard guard(h->device);
     const int K = h->K;
     uint64_t first, last, bound = 0;
-    const uint64_t *d_off;
-    if (!is_device_ptr(offsets)) {
-        first = offsets[0];
-        last = offsets[nreads];
-        for (uint64_t r = 0; r < nreads; ++r) {
-            const uint64_t s = offsets[r], e = offsets[r + 1];
-            if (e < s) return KMERCO_EINVAL;
-            if (e - s >= (uint64_t)K) bound += e - s - K + 1;
-        }
+    const uint64_t *d_off = offsets;
+    if (!is_device_ptr(offsets)) {   // host offsets: checked and summed on the device too
         KM_TRY(ensure(h, &h->in_offsets, &h->in_offsets_cap, nreads + 1));
         KM_CUDA(cudaMemcpyAsync(h->in_offsets, offsets, (nreads + 1) * 8, cudaMemcpyHostToDevice,
                                 h->stream));
         d_off = h->in_offsets;
-    } else {
-        KM_CUDA(cudaMemsetAsync(&h->ctr->bound, 0, sizeof(h->ctr->bound), h->stream));
-        KM_CUDA(cudaMemsetAsync(&h->ctr->bad_offsets, 0, sizeof(h->ctr->bad_offsets), h->stream));
-        KM_CUDA(launch_window_bound(offsets, nreads, K, h->ctr, h->stream));
-        h->launches += 1;
-        KM_TRY(read_counters(h));
-        if (h->ctr_host->bad_offsets) return KMERCO_EINVAL;
-        first = h->ctr_host->first;
-        last = h->ctr_host->last;
-        bound = h->ctr_host->bound;
-        d_off = offsets;
     }
+    KM_CUDA(cudaMemsetAsync(&h->ctr->bound, 0, sizeof(h->ctr->bound), h->stream));
+    KM_CUDA(cudaMemsetAsync(&h->ctr->bad_offsets, 0, sizeof(h->ctr->bad_offsets), h->stream));
+    KM_CUDA(launch_window_bound(d_off, nreads, K, h->ctr, h->stream));
+    h->launches += 1;
+    KM_TRY(read_counters(h));
+    if (h->ctr_host->bad_offsets) return KMERCO_EINVAL;
+    first = h->ctr_host->first;
+    last = h->ctr_host->last;
+    bound = h->ctr_host->bound;
     if (h->whole_file)   // the reads are one sequence of last - first bases
         bound = last - first >= (uint64_t)K ? last - first - K + 1 : 0;
     const uint64_t nbytes = last - first;
@@ -469,115 +590,18 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     if (bound == 0) return KMERCO_OK;   // no window fits in any read
     KM_TRY(ensure_set_capacity(h, bound));
 
-    // Partitioned design: size the increment-code buffers for one pass of at
-    // most kMaxBatchCodes increments; larger inputs run in several passes over
-    // consecutive chunk ranges (the atomic design takes over when the buffers
-    // cannot be had).
-    bool part = use_partitioned(h);
-    int coarse_shift = 0, slice_shift = 0;
-    uint64_t coarse_cap = 0, fine_cap = 0, nslices = 0, passes = 1;
-    bool repart = false, count = false;
-    if (part) {
-        const uint64_t W = h->G.words, U = bound * (uint64_t)h->nhash;
-        const uint64_t part_chunks = (nbytes + kPartChunk - 1) / kPartChunk;
-        passes = (U + h->pass_codes - 1) / h->pass_codes;
-        if (passes > part_chunks) passes = part_chunks;   // a pass takes one chunk at least
-        if (passes < 1) passes = 1;
-        const uint64_t Up = (U + passes - 1) / passes;   // increments per pass, on average
-        coarse_shift = ceil_log2(W) - 6;
-        if (coarse_shift < 0) coarse_shift = 0;
-        // counting apply for alpha <= 15: slices of kCountLanes / eta cells
-        // (rounded down to a power of two); compare-and-swap apply otherwise,
-        // or when the slices would be too many for one coarse region
-        int count_shift = 0;
-        while ((2ull << count_shift) * (uint64_t)h->eta <= (uint64_t)kCountLanes) ++count_shift;
-        count = h->alpha <= 15 &&
-                coarse_shift - count_shift <= kMaxCoarseShift - kSliceShift;
-        slice_shift = count ? count_shift : kSliceShift;
-        repart = coarse_shift > slice_shift;
-        if (!repart) slice_shift = coarse_shift;
-        nslices = (W + (1ull << slice_shift) - 1) >> slice_shift;
-        coarse_cap = Up / kCoarseBins;
-        coarse_cap = (coarse_cap + coarse_cap / 6 + 4096 + 3) & ~3ull;   // multiple of 4 codes
-        fine_cap = repart ? Up / nslices : 0;
-        fine_cap = (fine_cap + fine_cap / 5 + 1024 + 3) & ~3ull;
-        if (ensure(h, &h->coarse, &h->coarse_alloc, kCoarseBins * coarse_cap) != KMERCO_OK ||
-            (repart && ensure(h, &h->fine, &h->fine_alloc, nslices * fine_cap) != KMERCO_OK) ||
-            ensure(h, &h->part_ctr, &h->part_ctr_alloc, 2 * kCoarseBins + 2 * nslices) != KMERCO_OK)
-            part = false;
-    }
-
-    const uint64_t chunk = part ? kPartChunk : kChunk;
-    const uint64_t nchunks = (nbytes + chunk - 1) / chunk;
-    if (!part) passes = 1;
-    KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, nchunks));
-    KM_CUDA(launch_first_read(d_off, nreads, first, nchunks, chunk, h->first_read, h->stream));
-    h->launches += nchunks ? 1 : 0;
-
-    InsertArgs a;
-    a.bases = d_bases;
-    a.offsets = d_off;
-    a.nreads = nreads;
-    a.first = first;
-    a.last = last;
-    a.first_read = h->first_read;
-    a.chunk_begin = 0;
-    a.nchunks = nchunks;
-    a.K = K;
-    a.canonical = h->canonical;
-    a.whole_file = h->whole_file;
-    a.G = h->G;
-    a.table = h->table;
-    a.cap = h->cap;
-    a.dlist = h->dlist;
-    a.dlist_cap = h->dlist_cap;
-    a.ctr = h->ctr;
-    a.part = part ? 1 : 0;
-    a.coarse_shift = coarse_shift;
-    a.coarse = h->coarse;
-    a.coarse_cap = coarse_cap;
-    a.coarse_cursor = h->part_ctr;
-    a.coarse_written = h->part_ctr ? h->part_ctr + kCoarseBins : nullptr;
+    PartPlan pp = plan_partition(h, bound, nbytes);
+    if (pp.part &&
+        (ensure(h, &h->coarse, &h->coarse_alloc, pp.coarse_words()) != KMERCO_OK ||
+         (pp.repart && ensure(h, &h->fine, &h->fine_alloc, pp.fine_words()) != KMERCO_OK) ||
+         ensure(h, &h->part_ctr, &h->part_ctr_alloc, pp.ctr_words()) != KMERCO_OK))
+        pp = PartPlan();   // the atomic design when the buffers cannot be had
+    const uint64_t chunk = pp.part ? kPartChunk : kChunk;
+    KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, (nbytes + chunk - 1) / chunk));
+    const InsertArgs a = sample_args(h, d_bases, d_off, nreads, first, last);
     KM_CUDA(cudaEventRecord(h->ev[0], h->stream));
-    for (uint64_t pass = 0; pass < passes; ++pass) {
-        a.chunk_begin = nchunks * pass / passes;
-        a.nchunks = nchunks * (pass + 1) / passes;
-        if (part)
-            KM_CUDA(cudaMemsetAsync(h->part_ctr, 0, (2 * kCoarseBins + 2 * nslices) * 8,
-                                    h->stream));
-        KM_CUDA(launch_insert(a, !part ? h->grid_atomic
-                                 : coarse_shift <= 20 ? h->grid_part : h->grid_wide, h->stream));
-        h->launches += a.nchunks > a.chunk_begin ? 1 : 0;
-        if (!part) continue;
-        unsigned long long *fine_cursor = h->part_ctr + 2 * kCoarseBins;
-        unsigned long long *fine_written = fine_cursor + nslices;
-        if (repart) {
-            PartArgs p;
-            p.G = h->G;
-            p.coarse_shift = coarse_shift;
-            p.slice_shift = slice_shift;
-            p.coarse = h->coarse;
-            p.coarse_cap = coarse_cap;
-            p.coarse_written = a.coarse_written;
-            p.fine = h->fine;
-            p.fine_cap = fine_cap;
-            p.fine_cursor = fine_cursor;
-            p.fine_written = fine_written;
-            p.ctr = h->ctr;
-            KM_CUDA(launch_repartition(p, h->stream));
-            h->launches += 1;
-        }
-        ApplyArgs ap;
-        ap.G = h->G;
-        ap.slice_shift = slice_shift;
-        ap.codes = repart ? h->fine : h->coarse;
-        ap.cap = repart ? fine_cap : coarse_cap;
-        ap.written = repart ? fine_written : a.coarse_written;
-        ap.ctr = h->ctr;
-        KM_CUDA(count ? launch_apply_count(ap, nslices, h->stream)
-                      : launch_apply(ap, nslices, h->stream));
-        h->launches += 1;
-    }
+    KM_TRY(launch_sample_insert(h, a, pp, PartBufs{h->coarse, h->fine, h->part_ctr}, h->stream,
+                                h->launches));
     KM_CUDA(cudaEventRecord(h->ev[1], h->stream));
     h->insert_timed = true;
     h->classified = false;
@@ -863,6 +887,8 @@ int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
 }  // extern "C"
 
 // ------------------------------------------------------------------ batches
+constexpr int kBatchStreams = 8;
+
 struct kmerco_batch {
     std::vector<kmerco_t *> h;
     int n, kw, device;
@@ -886,6 +912,16 @@ struct kmerco_batch {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     cudaEvent_t ev[2];
+    // per-sample schedule: each sample's own insert kernels (partitioned
+    // design where it applies) on one of `streams` concurrent streams
+    int sched;                               // 0 persistent launch, 1 per-sample kernels
+    int streams;
+    cudaStream_t aux[kBatchStreams];
+    cudaEvent_t fork, join[kBatchStreams];
+    PartBufs bufs[kBatchStreams];            // increment-code scratch of each stream
+    uint64_t buf_words[kBatchStreams][3];    // their sizes (coarse, fine, counters)
+    std::vector<PartPlan> plans;             // per sample
+    std::vector<uint64_t> load;              // per sample: windows, for stream assignment
 };
 
 namespace {
@@ -947,6 +983,91 @@ int batch_launch(kmerco_batch *b, int chunk, int bpm) {
                                 b->sms * bpm, b->stream));
     b->launches += b->total_chunks ? 2 : 0;
     return KMERCO_OK;
+}
+
+// Streams of the per-sample schedule: each sample to the least loaded of
+// `S` streams, largest samples first.
+std::vector<int> batch_assign(const kmerco_batch *b, int S) {
+    std::vector<int> order(b->n), out(b->n, 0);
+    for (int i = 0; i < b->n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return b->load[x] > b->load[y]; });
+    std::vector<uint64_t> acc(S, 0);
+    for (int i : order) {
+        int k = 0;
+        for (int j = 1; j < S; ++j)
+            if (acc[j] < acc[k]) k = j;
+        out[i] = k;
+        acc[k] += b->load[i];
+    }
+    return out;
+}
+
+// Scratch of every stream, sized for the largest plan of any sample (so any
+// assignment fits).  Returns false when it cannot be had.
+bool batch_alloc_scratch(kmerco_batch *b) {
+    uint64_t need[3] = {0, 0, 0};
+    for (const PartPlan &pp : b->plans) {
+        if (!pp.part) continue;
+        need[0] = std::max(need[0], pp.coarse_words());
+        need[1] = std::max(need[1], pp.fine_words());
+        need[2] = std::max(need[2], pp.ctr_words());
+    }
+    for (int k = 0; k < kBatchStreams; ++k) {
+        if (!b->aux[k] && cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking) != cudaSuccess)
+            return false;
+        if (!b->join[k] && cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming) != cudaSuccess)
+            return false;
+        void **ptrs[3] = {(void **)&b->bufs[k].coarse, (void **)&b->bufs[k].fine,
+                          (void **)&b->bufs[k].ctr};
+        const uint64_t elem[3] = {4, 4, 8};
+        for (int q = 0; q < 3; ++q) {
+            if (b->buf_words[k][q] >= need[q]) continue;
+            cudaFree(*ptrs[q]);
+            *ptrs[q] = nullptr;
+            b->buf_words[k][q] = 0;
+            if (cudaMalloc(ptrs[q], need[q] * elem[q]) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            b->buf_words[k][q] = need[q];
+        }
+    }
+    return b->fork || cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+}
+
+// Per-sample schedule on S streams forked from and joined back into the
+// batch stream (capturable: no host synchronisation).
+int batch_launch_sliced(kmerco_batch *b, int S, bool reset) {
+    const std::vector<int> where = batch_assign(b, S);
+    KM_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (int k = 0; k < S; ++k) KM_CUDA(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+    for (int i = 0; i < b->n; ++i) {
+        kmerco_t *h = b->h[i];
+        cudaStream_t st = b->aux[where[i]];
+        if (reset) {
+            KM_CUDA(cudaMemsetAsync(h->G.cells, 0, h->G.words * 8, st));
+            if (h->table) KM_CUDA(cudaMemsetAsync(h->table, 0xFF, h->cap * h->kw * 8, st));
+            KM_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), st));
+        }
+        const unsigned long long *bo = &b->bound_host[(size_t)i * kBoundOutWords];
+        const bool any = h->whole_file ? bo[2] - bo[1] >= (uint64_t)h->K : bo[0] != 0;
+        if (!any) continue;
+        const InsertArgs a = sample_args(h, (const uint8_t *)b->p_bases[i] + bo[1], b->p_offs[i],
+                                         b->p_nreads[i], bo[1], bo[2]);
+        KM_TRY(launch_sample_insert(h, a, b->plans[i], b->bufs[where[i]], st, b->launches));
+    }
+    for (int k = 0; k < S; ++k) {
+        KM_CUDA(cudaEventRecord(b->join[k], b->aux[k]));
+        KM_CUDA(cudaStreamWaitEvent(b->stream, b->join[k], 0));
+    }
+    return KMERCO_OK;
+}
+
+// The chosen schedule: the persistent launch, or the per-sample kernels.
+int batch_run(kmerco_batch *b, bool reset) {
+    if (b->sched == 1) return batch_launch_sliced(b, b->streams, reset);
+    if (reset) KM_TRY(batch_reset_device(b));
+    return batch_launch(b, b->chunk, b->bpm);
 }
 
 void batch_mark_inserted(kmerco_batch *b) {
@@ -1018,6 +1139,14 @@ void kmerco_batch_destroy(kmerco_batch_t *b) {
         cudaFree(b->d_nreads);
         for (int i = 0; i < 2; ++i)
             if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+        for (int k = 0; k < kBatchStreams; ++k) {
+            cudaFree(b->bufs[k].coarse);
+            cudaFree(b->bufs[k].fine);
+            cudaFree(b->bufs[k].ctr);
+            if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+            if (b->join[k]) cudaEventDestroy(b->join[k]);
+        }
+        if (b->fork) cudaEventDestroy(b->fork);
         cudaGetLastError();
     }
     delete b;
@@ -1071,6 +1200,8 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
             return KMERCO_EINVAL;
     }
     // capacities (host work; never inside a capture)
+    b->plans.assign(b->n, PartPlan());
+    b->load.assign(b->n, 0);
     for (int i = 0; i < b->n; ++i) {
         kmerco_t *h = b->h[i];
         if (reset) KM_TRY(kmerco_reset(h));
@@ -1081,8 +1212,12 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
         KM_TRY(ensure_set_capacity(h, bound));
         const uint64_t most = (bo[2] - bo[1] + 1023) / 1024;   // chunks at the smallest chunk size
         KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, most ? most : 1));
+        b->plans[i] = plan_partition(h, bound, bo[2] - bo[1]);
+        b->load[i] = bound;
     }
     KM_CUDA(cudaStreamSynchronize(b->stream));
+    const bool sliced_ok = batch_alloc_scratch(b);
+    if (!sliced_ok) b->sched = 0;   // the persistent schedule needs no scratch
     b->planned = true;
     // autotune once per batch: chunk size x resident blocks, timed on this input
     if (reset && !b->tuned) {
@@ -1106,6 +1241,22 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
                 }
             }
         }
+        b->sched = 0;
+        // the per-sample schedule on 1, 2, 4 or 8 streams
+        for (int S = 1; sliced_ok && S <= kBatchStreams; S *= 2) {
+            KM_TRY(batch_reset_device(b));
+            KM_CUDA(cudaEventRecord(b->ev[0], b->stream));
+            KM_TRY(batch_launch_sliced(b, S, false));
+            KM_CUDA(cudaEventRecord(b->ev[1], b->stream));
+            KM_CUDA(cudaEventSynchronize(b->ev[1]));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+            if (ms < best) {
+                best = ms;
+                b->sched = 1;
+                b->streams = S;
+            }
+        }
         b->tuned = true;
         b->tuned_ms = best;
     }
@@ -1115,11 +1266,9 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
         // a stream that cannot be captured, such as the legacy default stream)
         if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
             cudaGetLastError();
-            KM_TRY(batch_reset_device(b));
-            KM_TRY(batch_launch(b, b->chunk, b->bpm));
+            KM_TRY(batch_run(b, true));
         } else {
-            int st = batch_reset_device(b);
-            if (st == KMERCO_OK) st = batch_launch(b, b->chunk, b->bpm);
+            int st = batch_run(b, true);
             cudaGraph_t g = nullptr;
             const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
             if (st != KMERCO_OK) {
@@ -1136,9 +1285,31 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
             KM_CUDA(cudaGraphLaunch(b->exec, b->stream));
         }
     } else {
-        KM_TRY(batch_launch(b, b->chunk, b->bpm));
+        KM_TRY(batch_run(b, false));
     }
     batch_mark_inserted(b);
+    return KMERCO_OK;
+}
+
+int kmerco_batch_schedule(kmerco_batch_t *b, int schedule, int streams) {
+    if (!b || schedule < -1 || schedule > 1) return KMERCO_EINVAL;
+    if (schedule == 1 && (streams < 1 || streams > kBatchStreams || (streams & (streams - 1))))
+        return KMERCO_EINVAL;
+    if (b->have_graph) {   // the captured graph follows the old schedule
+        DeviceGuard guard(b->device);
+        cudaStreamSynchronize(b->stream);
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->have_graph = false;
+    }
+    if (schedule < 0) {
+        b->tuned = false;
+        return KMERCO_OK;
+    }
+    b->tuned = true;
+    b->tuned_ms = 0;
+    b->sched = schedule;
+    b->streams = schedule == 1 ? streams : 0;
     return KMERCO_OK;
 }
 
@@ -1159,6 +1330,8 @@ int kmerco_batch_info(kmerco_batch_t *b, kmerco_batch_info_t *info) {
     info->graph = b->have_graph ? 1 : 0;
     info->launches = b->launches;
     info->total_chunks = b->total_chunks;
+    info->schedule = b->sched;
+    info->streams = b->sched == 1 ? b->streams : 0;
     return KMERCO_OK;
 }
 

@@ -721,8 +721,7 @@ __device__ __forceinline__ void repart_scan(const unsigned *v, unsigned *out, un
 // slices per region (2^(coarse_shift - kSliceShift)).
 template <int MAXF>
 __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p) {
-    extern __shared__ uint32_t rp_smem[];
-    uint32_t *staged = rp_smem, *sorted = rp_smem + kRepartTile;
+    extern __shared__ uint32_t sorted[];   // the tile's codes grouped by slice
     __shared__ unsigned hist[MAXF], start[MAXF], fill[MAXF];
     __shared__ unsigned long long base[MAXF];
     const unsigned b = blockIdx.y, tid = threadIdx.x;
@@ -759,12 +758,8 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
     for (int j = 0; j < 4; ++j) {
         const unsigned i = 4 * (tid + j * kRepartThreads);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (i + q < cnt) {
-                staged[i + q] = c16[4 * j + q];
-                atomicAdd(&hist[c16[4 * j + q] >> fsh], 1u);
-            }
-        }
+        for (int q = 0; q < 4; ++q)
+            if (i + q < cnt) atomicAdd(&hist[c16[4 * j + q] >> fsh], 1u);
     }
     __syncthreads();
     if (MAXF <= 64) {
@@ -790,10 +785,17 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
         base[f] = b0;
     }
     __syncthreads();
-    for (unsigned i = tid; i < cnt; i += kRepartThreads) {
-        const uint32_t code = staged[i];
-        const unsigned f = code >> fsh;
-        sorted[start[f] + atomicAdd(&fill[f], 1u)] = code;
+    // group the codes by slice, straight from registers
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const unsigned i = 4 * (tid + j * kRepartThreads);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i + q < cnt) {
+                const unsigned f = c16[4 * j + q] >> fsh;
+                sorted[start[f] + atomicAdd(&fill[f], 1u)] = c16[4 * j + q];
+            }
+        }
     }
     __syncthreads();
     const uint32_t smask = (1u << p.slice_shift) - 1;
@@ -884,7 +886,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
 // it past that bound by at most the increments in flight in the block
 // (kApplyThreads * 8), which stays below 2^16 for alpha <= 15.  Then every
 // counter becomes min(old + count, 2^alpha - 1) and the slice is written back.
-__global__ void __launch_bounds__(kApplyThreads, 1) apply_count_kernel(ApplyArgs p) {
+__global__ void __launch_bounds__(kApplyThreads, 2) apply_count_kernel(ApplyArgs p) {
     extern __shared__ uint32_t lanes[];   // two 16-bit counts per word
     const uint64_t s = blockIdx.x;
     const uint64_t n = p.written[s];
@@ -1049,7 +1051,7 @@ cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s) {
     if (p.coarse_shift - p.slice_shift > kMaxCoarseShift - kSliceShift ||
         p.coarse_shift <= p.slice_shift)
         return cudaErrorInvalidValue;
-    const int smem = 2 * kRepartTile * (int)sizeof(uint32_t);
+    const int smem = kRepartTile * (int)sizeof(uint32_t);
     const dim3 grid((unsigned)tiles, kCoarseBins);
     cudaError_t e;
     if (p.coarse_shift - p.slice_shift <= 6) {

@@ -310,9 +310,9 @@ cudaError_t launch_insert_batch(const InsertArgs *args, const unsigned long long
                                 int grid, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
 // Counting apply (alpha <= 15): the slice's increments are first counted in
-// 16-bit shared-memory lanes (2^slice_shift * eta of them, at most 65536),
+// 16-bit shared-memory lanes (2^slice_shift * eta of them, at most kCountLanes),
 // then added to the counters with saturation.
-constexpr int kCountLanes = 65536;
+constexpr int kCountLanes = 32768;
 cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
 // Insert n keys into a distinct set; when dlist is not null, keys new to the
 // set are appended to it (ctr->distinct counts them).

@@ -43,13 +43,15 @@ def _dev(a):
     return t
 
 
-def _run_batch(samples, K, stream, reset_twice=False, accumulate=False):
+def _run_batch(samples, K, stream, reset_twice=False, accumulate=False, schedule=None):
     filters = [kc.CountBF(K, m, alpha, nhash, tau, stream=stream.cuda_stream)
                for (_, _, m, alpha, nhash, tau) in samples]
     dev = [(_dev(b), _dev(o)) for (b, o, *_rest) in samples]
     torch.cuda.synchronize()
     nreads = [len(o) - 1 for (_, o, *_r) in samples]
     with kc.Batch(filters) as batch:
+        if schedule is not None:
+            batch.schedule(*schedule)
         kc.kmerco_batch_insert(batch.b, [d[0] if n else None for d, n in zip(dev, nreads)],
                                [d[1] for d in dev], nreads, reset=not accumulate)
         if reset_twice or accumulate:
@@ -72,9 +74,23 @@ def test_batch_matches_oracle_per_sample(K):
     stream = torch.cuda.Stream()
     results, info = _run_batch(samples, K, stream)
     assert info["samples"] == len(samples) and info["tuned"] == 1
-    assert info["chunk"] in (1024, 2048) and info["blocks_per_sm"] >= 2
+    assert info["schedule"] in (0, 1)
+    if info["schedule"] == 0:
+        assert info["chunk"] in (1024, 2048) and info["blocks_per_sm"] >= 2
+    else:
+        assert info["streams"] in (1, 2, 4, 8)
     for (b, o, m, alpha, nhash, tau), g in zip(samples, results):
         check(g, b, o, K, alpha, nhash, tau)
+
+
+@pytest.mark.parametrize("schedule", [(0, 0), (1, 1), (1, 4), (1, 8)])
+def test_every_batch_schedule_matches_oracle(schedule):
+    samples = _samples()
+    stream = torch.cuda.Stream()
+    results, info = _run_batch(samples, 31, stream, reset_twice=True, schedule=schedule)
+    assert (info["schedule"], info["streams"]) == schedule and info["graph"] == 1
+    for (b, o, m, alpha, nhash, tau), g in zip(samples, results):
+        check(g, b, o, 31, alpha, nhash, tau)
 
 
 def test_batch_graph_replay_gives_the_same_results():
@@ -107,6 +123,11 @@ def test_batch_rejects_bad_arguments():
         with pytest.raises(kc.KmercoError) as e:
             kc.Batch(hs)
         assert e.value.status == kc.EINVAL
+    with kc.Batch([a]) as batch:
+        for bad in ((2, 0), (1, 0), (1, 3), (1, 16), (-2, 0)):
+            with pytest.raises(kc.KmercoError) as e:
+                batch.schedule(*bad)
+            assert e.value.status == kc.EINVAL
     bases, offs = readsim.random_reads(10, 50, 60, seed=1)
     with kc.Batch([a]) as batch, pytest.raises(kc.KmercoError) as e:
         batch.insert([bases], [offs])   # host pointers
