@@ -324,7 +324,10 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
  * cannot be allocated.  Errors: EINVAL. */
 int kmerco_batch_schedule(kmerco_batch_t *b, int schedule, int streams);
 
-/* kmerco_classify() of every handle of the batch, in order. */
+/* Classification of every handle of the batch (the results of
+ * kmerco_classify on each): every sample's sort, query and split launched
+ * on the batch's concurrent streams with one readback before and one after;
+ * handle by handle when the batch has not set up its streams yet. */
 int kmerco_batch_classify(kmerco_batch_t *b);
 
 /* Schedule and counters of the batch. */

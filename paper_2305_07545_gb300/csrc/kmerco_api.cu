@@ -1315,7 +1315,77 @@ int kmerco_batch_schedule(kmerco_batch_t *b, int schedule, int streams) {
 
 int kmerco_batch_classify(kmerco_batch_t *b) {
     if (!b) return KMERCO_EINVAL;
-    for (kmerco_t *h : b->h) KM_TRY(kmerco_classify(h));
+    DeviceGuard guard(b->device);
+    // one readback of every sample's totals
+    for (kmerco_t *h : b->h)
+        KM_CUDA(cudaMemcpyAsync(h->ctr_host, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                b->stream));
+    KM_CUDA(cudaStreamSynchronize(b->stream));
+    std::vector<uint64_t> D(b->n, 0);
+    for (int i = 0; i < b->n; ++i) {
+        kmerco_t *h = b->h[i];
+        if (h->classified) continue;
+        KM_TRY(device_error_status(h->ctr_host->error));
+        D[i] = h->ctr_host->distinct;
+        if (D[i] >= 0xFFFFFFFFull) return KMERCO_ENOMEM;   // sort tiles index keys with 32 bits
+        const int kw = h->kw;
+        KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, D[i] * kw));
+        KM_TRY(ensure(h, &h->alt1, &h->alt1_cap, D[i] * kw));
+        KM_TRY(ensure(h, &h->est, &h->est_cap, D[i]));
+        KM_TRY(ensure(h, &h->split, &h->split_cap, D[i] * kw));
+        KM_TRY(ensure(h, &h->sort_scratch, &h->sort_scratch_cap, sort_scratch_words(D[i], kw)));
+        KM_TRY(ensure(h, &h->split_scratch, &h->split_scratch_cap, split_scratch_words(D[i])));
+    }
+    bool streams_ok = b->fork != nullptr;
+    for (int k = 0; streams_ok && k < kBatchStreams; ++k) streams_ok = b->aux[k] && b->join[k];
+    if (!streams_ok) {   // no per-sample streams were set up: one handle at a time
+        for (kmerco_t *h : b->h) KM_TRY(kmerco_classify(h));
+        return KMERCO_OK;
+    }
+    // every sample's radix sort, query and split, the samples spread over the
+    // streams by distinct count (no host synchronisation in between)
+    std::vector<int> order(b->n);
+    for (int i = 0; i < b->n; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return D[x] > D[y]; });
+    std::vector<uint64_t> acc(kBatchStreams, 0);
+    KM_CUDA(cudaEventRecord(b->fork, b->stream));
+    for (int k = 0; k < kBatchStreams; ++k) KM_CUDA(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+    for (int i : order) {
+        kmerco_t *h = b->h[i];
+        if (h->classified) continue;
+        int k = 0;
+        for (int j = 1; j < kBatchStreams; ++j)
+            if (acc[j] < acc[k]) k = j;
+        acc[k] += D[i] + 4096;
+        cudaStream_t st = b->aux[k];
+        const int bits = 2 * h->K, passes = (bits + kRadixBits - 1) / kRadixBits;
+        const uint64_t *sorted = h->dlist;
+        KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D[i], h->kw, bits, h->sort_scratch,
+                           &sorted, st));
+        KM_CUDA(launch_query(sorted, D[i], h->kw, h->K, h->G, h->est, st));
+        KM_CUDA(launch_split(sorted, h->est, D[i], h->kw, h->tau, h->split, h->split_scratch,
+                             h->ctr, st));
+        const uint64_t n_launch = (D[i] > 1 ? 3 * (uint64_t)passes : 0) + (D[i] ? 4 : 0);
+        h->launches += n_launch;
+        b->launches += n_launch;
+        h->sorted = sorted;
+        h->n_distinct = D[i];
+    }
+    for (int k = 0; k < kBatchStreams; ++k) {
+        KM_CUDA(cudaEventRecord(b->join[k], b->aux[k]));
+        KM_CUDA(cudaStreamWaitEvent(b->stream, b->join[k], 0));
+    }
+    // one readback of every sample's trustworthy count
+    for (kmerco_t *h : b->h)
+        KM_CUDA(cudaMemcpyAsync(h->ctr_host, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                b->stream));
+    KM_CUDA(cudaStreamSynchronize(b->stream));
+    for (kmerco_t *h : b->h) {
+        if (h->classified) continue;
+        h->n_trusted = h->ctr_host->trusted;
+        h->classified = true;
+        h->classify_timed = false;
+    }
     return KMERCO_OK;
 }
 

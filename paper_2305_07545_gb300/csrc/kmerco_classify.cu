@@ -232,22 +232,37 @@ __global__ void query_kernel(const uint64_t *keys, uint64_t n, int K, Geometry G
         const uint64_t klo = keys[i * KW];
         const uint64_t khi = KW == 2 ? keys[i * KW + 1] : 0;
         const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
+        // k_h counters in groups of four, the four loads in flight together;
+        // the minimum, or 0 as soon as one counter is 0 (Algorithm 5)
         uint64_t best = ~0ull;
-        for (int a = 0; a < G.nhash; ++a) {
-            uint64_t h1, h2;
-            if (KW == 1)
-                murmur8(k1m, (uint32_t)a, h1, h2);
-            else
-                murmur16(klo, khi, (uint32_t)a, h1, h2);
-            uint64_t cell;
-            unsigned slot;
-            address(G, h1, cell, slot);
-            const uint64_t v = (__ldg(G.cells + cell) >> (slot * (unsigned)G.alpha)) & G.maxc;
-            if (v == 0) {
-                best = 0;
-                break;
+        for (int a0 = 0; a0 < G.nhash && best; a0 += 4) {
+            uint64_t cell[4], word[4];
+            unsigned sh[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cell[j] = 0;
+                sh[j] = 0;
+                if (a0 + j < G.nhash) {
+                    uint64_t h1, h2;
+                    if (KW == 1)
+                        murmur8(k1m, (uint32_t)(a0 + j), h1, h2);
+                    else
+                        murmur16(klo, khi, (uint32_t)(a0 + j), h1, h2);
+                    unsigned slot;
+                    address(G, h1, cell[j], slot);
+                    sh[j] = slot * (unsigned)G.alpha;
+                }
             }
-            best = v < best ? v : best;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (a0 + j < G.nhash) word[j] = __ldg(G.cells + cell[j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (a0 + j < G.nhash) {
+                    const uint64_t v = (word[j] >> sh[j]) & G.maxc;
+                    best = v < best ? v : best;
+                }
+            }
         }
         est[i] = (uint32_t)best;
         (void)K;
