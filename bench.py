@@ -35,7 +35,7 @@ METRIC = "K-mer insertions/sec on 1 GB300 (bit-exact vs oracle); % of L2-atomic/
 UNIT = "K-mer insertions/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "insert_kernel_single.md")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "insert_phase_single.md")
 INSERT_SOURCES = [os.path.join(ROOT, "paper_2305_07545_gb300", "csrc", f)
                   for f in ("kmerco_insert.cu", "kmerco_internal.cuh")]
 
@@ -333,7 +333,9 @@ def run_ours(args) -> None:
     traffic = recorded_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "insert_kernel (fused pack/canonical/hash/countBF update/distinct set)",
+                "kernel": "insert phase: every kernel of one kmerco_insert call (insert_kernel: "
+                          "pack, canonical, hash, distinct set, increment staging; in the "
+                          "partitioned design also repartition_kernel and the apply kernel)",
                 "algorithmic_bytes_per_launch": int(launch_bytes),
                 "avg_launch_ms": avg_insert_ms, "insert_share_of_step": avg_insert_ms / (total_ms / args.steps),
                 "peak_source": peak_src}

@@ -263,6 +263,23 @@ int kmerco_classify_noalloc(const uint64_t *cells, uint64_t m, int k, int counte
                             int nhash, uint32_t threshold, const uint64_t *keys, uint64_t n,
                             uint32_t *est, uint64_t *out, uint64_t *n_trusted, void *stream);
 
+/*
+ * Persistence: a countBF and its distinct keys can be saved with
+ * kmerco_get_counters / kmerco_get_distinct and restored into a handle of
+ * the same parameters with these two calls (the paper keeps the countBF for
+ * later membership and frequency queries, Section 1).
+ * kmerco_set_counters: replace the countBF's cells with src (host or device,
+ *   nwords == stats.words, the layout of kmerco_get_counters).  ESIZE when
+ *   nwords differs.
+ * kmerco_add_distinct: add n keys (host or device, the layout of
+ *   kmerco_get_distinct: one uint64 each for K <= 32, [lo, hi] pairs
+ *   otherwise) to the distinct set; keys already present are ignored.
+ *   The window totals of kmerco_stats are not restored.
+ * Both leave the handle unclassified.  Errors: EINVAL, ESIZE, ENOMEM, ECUDA.
+ */
+int kmerco_set_counters(kmerco_t *h, const uint64_t *src, uint64_t nwords);
+int kmerco_add_distinct(kmerco_t *h, const uint64_t *keys, uint64_t n);
+
 /* Zero the countBF, empty the distinct set and all totals; keeps memory. */
 int kmerco_reset(kmerco_t *h);
 

@@ -235,7 +235,7 @@ uint64_t oracle_extract(const uint8_t *bases, const uint64_t *offsets,
 }
 
 /*
- * H_a(K-mer) (Section 3, Algorithm 3 line "h <- H_a(Read)"): MurmurHash3
+ * H_a(K-mer) (Section 3; the hash step of Algorithm 3): MurmurHash3
  * x64_128 of the key's bytes with seed a, first output word.  Key bytes:
  * K <= 32 -> the 8 bytes of lo, little-endian; K > 32 -> the 8 bytes of lo
  * then the 8 bytes of hi, each little-endian.

@@ -86,6 +86,8 @@ SIGNATURES = {
     "kmerco_batch_create": (c_int, [POINTER(c_void_p), c_int, POINTER(c_void_p)]),
     "kmerco_batch_destroy": (None, [c_void_p]),
     "kmerco_batch_insert": (c_int, [c_void_p, POINTER(c_void_p), POINTER(c_void_p), _u64p, c_int]),
+    "kmerco_set_counters": (c_int, [c_void_p, c_void_p, c_uint64]),
+    "kmerco_add_distinct": (c_int, [c_void_p, c_void_p, c_uint64]),
     "kmerco_batch_classify": (c_int, [c_void_p]),
     "kmerco_batch_schedule": (c_int, [c_void_p, c_int, c_int]),
     "kmerco_batch_info": (c_int, [c_void_p, c_void_p]),
@@ -224,6 +226,14 @@ def kmerco_merge(dst: int, src: int) -> None:
     _check(load().kmerco_merge(dst, src), "kmerco_merge")
 
 
+def kmerco_set_counters(h: int, src, nwords: int) -> None:
+    _check(load().kmerco_set_counters(h, _ptr(src), nwords), "kmerco_set_counters")
+
+
+def kmerco_add_distinct(h: int, keys, n: int) -> None:
+    _check(load().kmerco_add_distinct(h, _ptr(keys), n), "kmerco_add_distinct")
+
+
 def kmerco_reset(h: int) -> None:
     _check(load().kmerco_reset(h), "kmerco_reset")
 
@@ -291,9 +301,45 @@ class CountBF:
         (Algorithm 3's addressing; ``m`` is then ignored)."""
         self.k = k
         self.kw = 1 if k <= 32 else 2
+        self.params = dict(k=k, m=m, counter_bits=counter_bits, nhash=nhash,
+                           threshold=threshold, forward_only=bool(forward_only),
+                           dims=tuple(dims) if dims is not None else None,
+                           canonical_hash=bool(canonical_hash), whole_file=bool(whole_file))
         self.h = kmerco_create_ex(k, m, counter_bits, nhash, threshold, forward_only, stream,
                                   hbm_budget, device, update_mode, dims, pass_codes,
                                   canonical_hash, whole_file)
+
+    def save(self, path: str) -> None:
+        """Write the countBF, its distinct keys and its parameters to an
+        ``.npz`` file (readable back with :meth:`load`)."""
+        self.classify()   # the distinct keys are read back after classification
+        keys, _ = self.distinct()
+        p = dict(self.params)
+        dims = p.pop("dims")
+        np.savez(path, cells=self.counters(), keys=keys,
+                 dims=np.array(dims if dims is not None else (0, 0), np.uint64),
+                 params=np.array([p["k"], p["m"], p["counter_bits"], p["nhash"], p["threshold"],
+                                  p["forward_only"], p["canonical_hash"], p["whole_file"]],
+                                 np.uint64))
+
+    @classmethod
+    def load(cls, path: str, **kw) -> "CountBF":
+        """A new handle holding the countBF and distinct keys of a saved file
+        (``kw``: options of the constructor that do not change the results,
+        such as ``stream`` or ``update_mode``)."""
+        z = np.load(path)
+        k, m, alpha, nhash, tau, fwd, ch, wf = (int(v) for v in z["params"])
+        dims = tuple(int(v) for v in z["dims"])
+        bf = cls(k, m, alpha, nhash, tau, forward_only=bool(fwd),
+                 dims=dims if dims[0] else None, canonical_hash=bool(ch), whole_file=bool(wf),
+                 **kw)
+        cells = np.ascontiguousarray(z["cells"], np.uint64)
+        kmerco_set_counters(bf.h, cells, len(cells))
+        keys = np.ascontiguousarray(z["keys"], np.uint64)
+        n = len(keys)
+        if n:
+            kmerco_add_distinct(bf.h, keys, n)
+        return bf
 
     def close(self) -> None:
         if self.h:

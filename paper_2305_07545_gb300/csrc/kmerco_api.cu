@@ -783,6 +783,37 @@ int kmerco_get_counters(kmerco_t *h, uint64_t *dst, uint64_t nwords) {
     return copy_out(h, dst, h->G.cells, h->G.words * 8);
 }
 
+int kmerco_set_counters(kmerco_t *h, const uint64_t *src, uint64_t nwords) {
+    if (!h || (!src && nwords)) return KMERCO_EINVAL;
+    if (nwords != h->G.words) return KMERCO_ESIZE;
+    DeviceGuard guard(h->device);
+    KM_CUDA(cudaMemcpyAsync(h->G.cells, src, nwords * 8, cudaMemcpyDefault, h->stream));
+    KM_CUDA(cudaStreamSynchronize(h->stream));
+    h->classified = false;
+    return KMERCO_OK;
+}
+
+int kmerco_add_distinct(kmerco_t *h, const uint64_t *keys, uint64_t n) {
+    if (!h || (!keys && n)) return KMERCO_EINVAL;
+    if (n == 0) return KMERCO_OK;
+    DeviceGuard guard(h->device);
+    const uint64_t words = n * h->kw;
+    const uint64_t *d_keys = keys;
+    if (!is_device_ptr(keys)) {   // stage host keys in the classification buffer
+        KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, words));
+        KM_CUDA(cudaMemcpyAsync(h->alt0, keys, words * 8, cudaMemcpyHostToDevice, h->stream));
+        d_keys = h->alt0;
+    }
+    KM_TRY(ensure_set_capacity(h, n));
+    KM_CUDA(launch_reinsert(d_keys, n, h->kw, h->table, h->cap, h->dlist, h->dlist_cap, h->ctr,
+                            h->stream));
+    h->launches += 1;
+    KM_TRY(read_counters(h));
+    KM_TRY(device_error_status(h->ctr_host->error));
+    h->classified = false;
+    return KMERCO_OK;
+}
+
 int kmerco_get_distinct(kmerco_t *h, uint64_t *keys, uint32_t *est, uint64_t cap, uint64_t *n) {
     if (!h || !n) return KMERCO_EINVAL;
     if (!h->classified) return KMERCO_ESTATE;
