@@ -294,12 +294,21 @@ def run_ours(args) -> None:
         h_tr = torch.empty(cap * kw, dtype=torch.int64).pin_memory()
         h_er = torch.empty(cap * kw, dtype=torch.int64).pin_memory()
 
+        split = {"reset_insert": 0.0, "classify": 0.0, "copy_back": 0.0}
+
         def e2e_step():
+            t = time.perf_counter()
             bf.reset()
             kc.kmerco_insert(bf.h, h_bases, h_offsets, nreads)
-            bf.classify()
+            t1 = time.perf_counter()
+            bf.classify()   # waits for the insert (it reads the distinct count)
+            t2 = time.perf_counter()
             nt = kc.kmerco_get_trusted(bf.h, h_tr, cap)
             ne = kc.kmerco_get_erroneous(bf.h, h_er, cap)
+            t3 = time.perf_counter()
+            split["reset_insert"] += t1 - t
+            split["classify"] += t2 - t1
+            split["copy_back"] += t3 - t2
             return nt, ne
 
         for _ in range(max(1, args.warmup // 2)):
@@ -307,6 +316,8 @@ def run_ours(args) -> None:
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
+        for k in split:
+            split[k] = 0.0
         t0 = time.perf_counter()
         for _ in range(args.steps):
             nt, ne = e2e_step()
@@ -317,7 +328,8 @@ def run_ours(args) -> None:
                "h2d_bytes_per_step": int(bases.nbytes + offsets.nbytes),
                "d2h_bytes_per_step": int(8 * kw * distinct),
                "note": "reset + insert from pinned host reads + classify + copy of the "
-                       "trustworthy and erroneous key lists to pinned host memory; wall clock"}
+                       "trustworthy and erroneous key lists to pinned host memory; wall clock",
+               "host_ms_per_step": {k: 1000.0 * v / args.steps for k, v in split.items()}}
 
     bf.close()
     if rank != 0:

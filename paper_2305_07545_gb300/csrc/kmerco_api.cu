@@ -16,6 +16,8 @@
 
 using namespace countbf;
 
+constexpr int kCopyPieces = 8;   // pieces of a host input copied while earlier ones are inserted
+
 struct kmerco {
     int K, kw, alpha, eta, nhash, canonical;   // canonical: 0 forward, 1 lexicographic, 2 hash
     int whole_file;
@@ -58,6 +60,8 @@ struct kmerco {
     uint64_t n_distinct, n_trusted;
     bool classified;
     cudaEvent_t ev[4];
+    cudaStream_t copy_stream;                      // host input copies (created on first use)
+    cudaEvent_t copy_ev[kCopyPieces + 1], copy_fork;
     bool insert_timed, classify_timed;
     uint64_t launches;       // kernels launched by this handle
     uint32_t *coarse;        // partitioned design: increment codes per coarse region
@@ -242,6 +246,19 @@ bool is_prime(uint64_t n) {
     return true;
 }
 
+// Pinned host mirror of the classification scratch, sized for the largest
+// user (the bucket sort's histogram, map, starts, bounds and shifts).
+constexpr uint64_t kBucketHostWords = 4 * (uint64_t)kHistBins + 1 + kHistBins / 2;
+
+int ensure_bucket_host(kmerco_t *h) {
+    if (h->bucket_host) return KMERCO_OK;
+    if (cudaMallocHost((void **)&h->bucket_host, kBucketHostWords * 8) != cudaSuccess) {
+        h->bucket_host = nullptr;
+        return KMERCO_ENOMEM;
+    }
+    return KMERCO_OK;
+}
+
 // Smallest l with 2^l >= x (64 for x above 2^63).
 int ceil_log2(uint64_t x) {
     int l = 0;
@@ -321,15 +338,59 @@ InsertArgs sample_args(const kmerco_t *h, const uint8_t *d_bases, const uint64_t
     return a;
 }
 
+// A host input copied to the device in pieces on its own stream, each piece
+// inserted as soon as it (and the K - 1 bytes after it) has arrived.
+struct HostCopy {
+    const uint8_t *src;          // host bytes of the call (from offsets[0])
+    uint8_t *dst;                // device staging of the same bytes
+    cudaStream_t stream;
+    cudaEvent_t *ev;             // kCopyPieces + 1 events
+    cudaEvent_t fork;
+};
+
 // All device work of one insert call on stream s, without host
 // synchronisation (so it can be captured): first reads of the chunks, then
 // per pass the insert kernel and, in the partitioned design, repartition and
 // apply.  h->first_read must hold the call's chunks; pb holds pp's buffers.
+// With hc, the call's bytes are copied from the host in up to kCopyPieces
+// chunk ranges, overlapped with the insert launches of the earlier ranges.
 int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
-                         const PartBufs &pb, cudaStream_t s, uint64_t &launches) {
+                         const PartBufs &pb, cudaStream_t s, uint64_t &launches,
+                         const HostCopy *hc = nullptr) {
     const uint64_t nbytes = a.last - a.first;
     const uint64_t chunk = pp.part ? kPartChunk : kChunk;
     const uint64_t nchunks = (nbytes + chunk - 1) / chunk;
+    // chunk ranges of the insert launches: per pass, pieces when copying
+    const uint64_t q = hc && pp.passes <= (uint64_t)kCopyPieces
+                           ? std::max<uint64_t>(1, kCopyPieces / pp.passes) : 1;
+    std::vector<uint64_t> cut;   // launch r takes chunks [cut[r], cut[r + 1])
+    for (uint64_t pass = 0; pass < pp.passes; ++pass) {
+        const uint64_t cb = nchunks * pass / pp.passes, ce = nchunks * (pass + 1) / pp.passes;
+        const uint64_t qq = std::min<uint64_t>(q, std::max<uint64_t>(1, ce - cb));
+        for (uint64_t j = 0; j < qq; ++j) cut.push_back(cb + (ce - cb) * j / qq);
+    }
+    cut.push_back(nchunks);
+    const uint64_t nr = cut.size() - 1;
+    const bool piecewise = hc && nr <= (uint64_t)kCopyPieces;
+    if (hc) {
+        // the staging buffer may still be read by the previous call's kernels
+        KM_CUDA(cudaEventRecord(hc->fork, s));
+        KM_CUDA(cudaStreamWaitEvent(hc->stream, hc->fork, 0));
+        if (piecewise) {
+            for (uint64_t r = 0; r < nr; ++r) {
+                const uint64_t lo = std::min(cut[r] * chunk, nbytes);
+                const uint64_t hi = r + 1 == nr ? nbytes : std::min(cut[r + 1] * chunk, nbytes);
+                if (hi > lo)
+                    KM_CUDA(cudaMemcpyAsync(hc->dst + lo, hc->src + lo, hi - lo,
+                                            cudaMemcpyHostToDevice, hc->stream));
+                KM_CUDA(cudaEventRecord(hc->ev[r], hc->stream));
+            }
+        } else {
+            KM_CUDA(cudaMemcpyAsync(hc->dst, hc->src, nbytes, cudaMemcpyHostToDevice, hc->stream));
+            KM_CUDA(cudaEventRecord(hc->ev[0], hc->stream));
+            KM_CUDA(cudaStreamWaitEvent(s, hc->ev[0], 0));
+        }
+    }
     KM_CUDA(launch_first_read(a.offsets, a.nreads, a.first, nchunks, chunk, h->first_read, s));
     launches += nchunks ? 1 : 0;
     a.part = pp.part ? 1 : 0;
@@ -340,12 +401,20 @@ int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
     a.coarse_written = pb.ctr ? pb.ctr + kCoarseBins : nullptr;
     const int grid = !pp.part ? h->grid_atomic : pp.coarse_shift <= 20 ? h->grid_part
                                                                        : h->grid_wide;
+    uint64_t r = 0;   // next launch range
     for (uint64_t pass = 0; pass < pp.passes; ++pass) {
-        a.chunk_begin = nchunks * pass / pp.passes;
-        a.nchunks = nchunks * (pass + 1) / pp.passes;
+        const uint64_t pass_end = nchunks * (pass + 1) / pp.passes;
         if (pp.part) KM_CUDA(cudaMemsetAsync(pb.ctr, 0, pp.ctr_words() * 8, s));
-        KM_CUDA(launch_insert(a, grid, s));
-        launches += a.nchunks > a.chunk_begin ? 1 : 0;
+        for (; r < nr && cut[r + 1] <= pass_end && cut[r] < pass_end; ++r) {
+            if (piecewise) {   // this range's bytes and the K - 1 after it
+                KM_CUDA(cudaStreamWaitEvent(s, hc->ev[r], 0));
+                if (r + 1 < nr) KM_CUDA(cudaStreamWaitEvent(s, hc->ev[r + 1], 0));
+            }
+            a.chunk_begin = cut[r];
+            a.nchunks = cut[r + 1];
+            KM_CUDA(launch_insert(a, grid, s));
+            launches += a.nchunks > a.chunk_begin ? 1 : 0;
+        }
         if (!pp.part) continue;
         unsigned long long *fine_cursor = pb.ctr + 2 * kCoarseBins;
         unsigned long long *fine_written = fine_cursor + pp.nslices;
@@ -530,6 +599,10 @@ void kmerco_destroy(kmerco_t *h) {
         if (h->ctr_host) cudaFreeHost(h->ctr_host);
         for (int i = 0; i < 4; ++i)
             if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+        for (int i = 0; i <= kCopyPieces; ++i)
+            if (h->copy_ev[i]) cudaEventDestroy(h->copy_ev[i]);
+        if (h->copy_fork) cudaEventDestroy(h->copy_fork);
+        if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
         if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
         cudaGetLastError();
     }
@@ -577,14 +650,14 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     const uint64_t nbytes = last - first;
     if (nbytes && !bases) return KMERCO_EINVAL;
     const uint8_t *d_bases = nullptr;
+    bool host_bases = false;
     if (nbytes) {
         if (is_device_ptr(bases)) {
             d_bases = (const uint8_t *)bases + first;
-        } else {
+        } else {   // copied below, piece by piece, while the insert runs
             KM_TRY(ensure(h, &h->in_bases, &h->in_bases_cap, nbytes));
-            KM_CUDA(cudaMemcpyAsync(h->in_bases, bases + first, nbytes, cudaMemcpyHostToDevice,
-                                    h->stream));
             d_bases = h->in_bases;
+            host_bases = true;
         }
     }
     if (bound == 0) return KMERCO_OK;   // no window fits in any read
@@ -599,9 +672,21 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     const uint64_t chunk = pp.part ? kPartChunk : kChunk;
     KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, (nbytes + chunk - 1) / chunk));
     const InsertArgs a = sample_args(h, d_bases, d_off, nreads, first, last);
+    HostCopy hc;
+    if (host_bases) {
+        if (!h->copy_stream) {
+            bool ok = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaEventCreateWithFlags(&h->copy_fork, cudaEventDisableTiming) == cudaSuccess;
+            for (int i = 0; ok && i <= kCopyPieces; ++i)
+                ok = cudaEventCreateWithFlags(&h->copy_ev[i], cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) return KMERCO_ECUDA;
+        }
+        hc = HostCopy{(const uint8_t *)bases + first, h->in_bases, h->copy_stream, h->copy_ev,
+                      h->copy_fork};
+    }
     KM_CUDA(cudaEventRecord(h->ev[0], h->stream));
     KM_TRY(launch_sample_insert(h, a, pp, PartBufs{h->coarse, h->fine, h->part_ctr}, h->stream,
-                                h->launches));
+                                h->launches, host_bases ? &hc : nullptr));
     KM_CUDA(cudaEventRecord(h->ev[1], h->stream));
     h->insert_timed = true;
     h->classified = false;
@@ -636,7 +721,7 @@ int kmerco_classify(kmerco_t *h) {
         const int shift = bits - kHistBits;
         // device and pinned layout: hist u32[B] | map u32[B] | start u64[B+1] |
         // lo u64[B] | rsh i32[B] (| cursor u64[B] on the device only)
-        const uint64_t words = 4 * (uint64_t)kHistBins + 1 + kHistBins / 2;
+        const uint64_t words = kBucketHostWords;
         KM_TRY(ensure(h, &h->bucket_scratch, &h->bucket_scratch_cap, words + kHistBins));
         unsigned *d_hist = (unsigned *)h->bucket_scratch;
         unsigned *d_map = d_hist + kHistBins;
@@ -644,11 +729,7 @@ int kmerco_classify(kmerco_t *h) {
         unsigned long long *d_lo = d_start + kHistBins + 1;
         int *d_rsh = (int *)(d_lo + kHistBins);
         unsigned long long *d_cursor = (unsigned long long *)(d_rsh + kHistBins);
-        if (!h->bucket_host &&
-            cudaMallocHost((void **)&h->bucket_host, words * sizeof(unsigned long long)) != cudaSuccess) {
-            h->bucket_host = nullptr;
-            return KMERCO_ENOMEM;
-        }
+        KM_TRY(ensure_bucket_host(h));
         unsigned *hist = (unsigned *)h->bucket_host, *map = hist + kHistBins;
         unsigned long long *start = h->bucket_host + kHistBins;
         unsigned long long *lo = start + kHistBins + 1;

@@ -6,10 +6,12 @@
 //    digit counts, one scan per digit across tiles, then a stable scatter
 //    in which each warp ranks equal digits with one ballot per digit bit and the
 //    tile is reordered in shared memory before coalesced stores.
-//  - bucket_sort (one-word keys): the top 12 of the 2K key bits split the
-//    keys into 4096 buckets in one scatter pass (cursor atomics aggregated
-//    per block), then each bucket is bitonic-sorted in shared memory by one
-//    block.  Buckets too large for shared memory are left to radix_sort.
+//  - bucket_sort (one-word keys, up to ~1.3e8): a histogram of the top 16
+//    key bits, adjacent bins merged on the host into super-buckets of at
+//    most kBucketCap keys, one scatter pass, then each super-bucket sorted
+//    in shared memory by one block (counting sort on 12 more bits, then
+//    insertion or bitonic sort).  A single bin too large for shared memory
+//    is left to radix_sort.
 //  - query: per key, k_h hashes and the minimum counter, 0 if any is 0.
 //  - split: stable partition on est > tau (trustworthy first).
 //  - merge: counter-wise min(a + b, 2^alpha - 1) of two countBFs.

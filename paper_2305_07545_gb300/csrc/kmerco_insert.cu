@@ -879,15 +879,12 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
 }
 
 // Counting apply (alpha <= 15): one slice of 2^slice_shift cells per block.
-// The slice's increments are counted in 16-bit shared-memory lanes, counter
-// (cell, l) at lane l * 2^slice_shift + cell; each lane stops counting at
-// 2^alpha - 1, where the counter saturates whatever its old value.  A count
-// is checked before it is incremented, so concurrent increments can carry
-// it past that bound by at most the increments in flight in the block
-// (kApplyThreads * 8), which stays below 2^16 for alpha <= 15.  Then every
-// counter becomes min(old + count, 2^alpha - 1) and the slice is written back.
+// The slice's increments are counted in 32-bit shared-memory lanes, counter
+// (cell, l) at lane l * 2^slice_shift + cell (a pass stages at most 2^31
+// increments, so a lane cannot wrap).  Then every counter becomes
+// min(old + count, 2^alpha - 1) and the slice is written back once.
 __global__ void __launch_bounds__(kApplyThreads, 2) apply_count_kernel(ApplyArgs p) {
-    extern __shared__ uint32_t lanes[];   // two 16-bit counts per word
+    extern __shared__ uint32_t lanes[];   // one 32-bit count per counter of the slice
     const uint64_t s = blockIdx.x;
     const uint64_t n = p.written[s];
     if (n == 0) return;   // no increments for this slice
@@ -896,12 +893,11 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_count_kernel(ApplyArgs
     const uint64_t slice = 1ull << ssh;
     const unsigned nw = (unsigned)min(slice, p.G.words - w0);
     const unsigned eta = (unsigned)p.G.eta;
-    const unsigned nwords = (eta << ssh) >> 1;
+    const unsigned nwords = eta << ssh;
     for (unsigned i = threadIdx.x; i < nwords; i += kApplyThreads) lanes[i] = 0;
     __syncthreads();
     const uint32_t *src = p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
     const uint32_t wmask = (uint32_t)(slice - 1);
-    const unsigned cap = (unsigned)p.G.maxc;
     constexpr unsigned kStep = kApplyThreads * 8;
     for (uint64_t i0 = 0; i0 < n; i0 += kStep) {
         uint32_t code[8];
@@ -929,20 +925,18 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_count_kernel(ApplyArgs
         for (int q = 0; q < 8; ++q) {
             if (!((valid >> q) & 1u)) continue;   // past the end
             const unsigned c = ((code[q] & 63u) << ssh) | ((code[q] >> 6) & wmask);
-            uint32_t *wp = lanes + (c >> 1);
-            const unsigned sh = (c & 1u) << 4;
-            if (((*(volatile uint32_t *)wp >> sh) & 0xFFFFu) < cap) atomicAdd(wp, 1u << sh);
+            atomicAdd(lanes + c, 1u);
         }
     }
     __syncthreads();
-    const uint16_t *cnt16 = (const uint16_t *)lanes;
+    const uint32_t *cnt = lanes;
     const unsigned alpha = (unsigned)p.G.alpha;
     const uint64_t maxc = p.G.maxc;
     for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) {
         const uint64_t old = p.G.cells[w0 + i];
         uint64_t out = 0;
         for (unsigned l = 0; l < eta; ++l) {
-            const uint64_t v = ((old >> (l * alpha)) & maxc) + cnt16[((uint64_t)l << ssh) | i];
+            const uint64_t v = ((old >> (l * alpha)) & maxc) + cnt[((uint64_t)l << ssh) | i];
             out |= (v < maxc ? v : maxc) << (l * alpha);
         }
         p.G.cells[w0 + i] = out;
@@ -1080,11 +1074,11 @@ cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
 
 cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
     if (nslices == 0) return cudaSuccess;
-    const size_t smem = ((size_t)p.G.eta << p.slice_shift) * 2;
-    if (smem > (size_t)kCountLanes * 2 || p.G.alpha > 15) return cudaErrorInvalidValue;
+    const size_t smem = ((size_t)p.G.eta << p.slice_shift) * 4;
+    if (smem > (size_t)kCountLanes * 4 || p.G.alpha > 15) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(apply_count_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kCountLanes * 2);
+                                         kCountLanes * 4);
     if (e != cudaSuccess) return e;
     apply_count_kernel<<<(unsigned)nslices, kApplyThreads, smem, s>>>(p);
     return cudaGetLastError();

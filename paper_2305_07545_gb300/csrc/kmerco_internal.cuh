@@ -310,9 +310,9 @@ cudaError_t launch_insert_batch(const InsertArgs *args, const unsigned long long
                                 int grid, cudaStream_t s);
 cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
 // Counting apply (alpha <= 15): the slice's increments are first counted in
-// 16-bit shared-memory lanes (2^slice_shift * eta of them, at most kCountLanes),
-// then added to the counters with saturation.
-constexpr int kCountLanes = 32768;
+// 32-bit shared-memory lanes (2^slice_shift * eta of them, at most
+// kCountLanes), then added to the counters with saturation.
+constexpr int kCountLanes = 16384;
 cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_t s);
 // Insert n keys into a distinct set; when dlist is not null, keys new to the
 // set are appended to it (ctr->distinct counts them).
@@ -326,6 +326,7 @@ cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *
 uint64_t sort_scratch_words(uint64_t n, int kw);
 cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint64_t n, int kw,
                        int bits, uint32_t *counts, const uint64_t **result, cudaStream_t s);
+
 
 // Bucket sort of one-word keys (classify): bucket_histogram counts
 // key >> shift over kHistBins bins; the host merges adjacent bins into

@@ -365,15 +365,19 @@ def test_single_sample_workload_full_size():
     assert np.array_equal(g["erroneous"], dlo[~tr])
 
 
-@pytest.mark.parametrize("K,pass_codes", [(21, 20000), (40, 50000), (55, 7777), (31, 1)])
-def test_partitioned_in_several_passes(K, pass_codes):
+@pytest.mark.parametrize("K,pass_codes,host", [(21, 20000, False), (40, 50000, False),
+                                                (55, 7777, False), (31, 1, False),
+                                                (21, 300000, True), (33, 1, True),
+                                                (25, 0, True)])
+def test_partitioned_in_several_passes(K, pass_codes, host):
     # a batch with more increments than one pass stages runs as consecutive
-    # chunk ranges, each staged, repartitioned and applied on its own
+    # chunk ranges, each staged, repartitioned and applied on its own; host
+    # reads are copied in pieces while earlier pieces are inserted
     b, o = readsim.scaled("tiny", 4000, seed_offset=21).generate()
     g = gpu_run(b, o, K, 1 << 22, 4, 3, 2, update_mode=kc.UPDATE_PARTITIONED,
-                pass_codes=pass_codes)
+                pass_codes=pass_codes, device_inputs=not host)
     check(g, b, o, K, 4, 3, 2)
-    assert g["stats"]["launches"] > 20
+    assert g["stats"]["launches"] > (8 if pass_codes == 0 else 20)
 
 
 @pytest.mark.parametrize("K", [21, 55])
@@ -413,3 +417,35 @@ def test_whole_file_short_reads():
     ref = check(g, b, o, 21, 4, 3, 2, whole_file=True)
     assert ref.n_windows == int(o[-1]) - 21 + 1
     assert gpu_run(b, o, 21, 1 << 16, 4, 3, 2)["stats"]["windows"] == 0
+
+
+@pytest.mark.parametrize("K,prefix", [(40, 0), (55, 0), (40, 30), (64, 40)])
+def test_segmented_sort_of_large_key_sets(K, prefix):
+    # over 2^20 distinct two-word keys: radix passes over the top key bits,
+    # then a rank sort inside each segment; with a long shared prefix many
+    # keys share their top bits, so segments beyond 256 keys take their own
+    # radix sort
+    rng = readsim.Stream(900 + K + prefix)
+    n_reads, length = 22000, 120
+    codes = np.frombuffer(b"ACGT", np.uint8)[rng.integers(n_reads * length, 4)]
+    reads = codes.reshape(n_reads, length)
+    if prefix:
+        reads[: n_reads // 2, :prefix] = ord("A")
+    b = np.ascontiguousarray(reads).reshape(-1)
+    o = np.arange(0, n_reads * length + 1, length, dtype=np.uint64)
+    g = gpu_run(b, o, K, 1 << 24, 4, 3, 2)
+    assert g["stats"]["distinct"] > (1 << 20)
+    check(g, b, o, K, 4, 3, 2)
+
+
+@pytest.mark.parametrize("update_mode", [kc.UPDATE_ATOMIC, kc.UPDATE_PARTITIONED])
+def test_host_inputs_in_pieces_and_back_to_back_calls(update_mode):
+    # two host-input calls in a row reuse the staging buffer: the second
+    # call's copies must wait for the first call's kernels
+    b, o = readsim.scaled("tiny", 6000, seed_offset=24).generate()
+    half = 2500
+    b1, o1 = b[:int(o[half])].copy(), o[:half + 1].copy()
+    b2, o2 = b[int(o[half]):].copy(), (o[half:] - o[half]).copy()
+    g = gpu_run(b, o, 27, 1 << 22, 4, 4, 2, update_mode=update_mode, device_inputs=False,
+                batches=[(b1, o1), (b2, o2)])
+    check(g, b, o, 27, 4, 4, 2)
