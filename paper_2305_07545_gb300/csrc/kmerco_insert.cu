@@ -344,16 +344,19 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
             if (PART) {
                 // stage one 32-bit code per increment, cell within the coarse
                 // region (up to 24 bits) above the counter within the cell
-                // (6 bits); the region itself goes beside it
+                // (6 bits); the region itself goes beside it.  The group's
+                // nh codes of a window sit together: one reservation per warp.
+                const unsigned nh = (unsigned)min(4, G.nhash - a0);
+                const unsigned bal = __ballot_sync(0xffffffffu, active);
+                unsigned base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&S.nupd, nh * (unsigned)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                base += nh * (unsigned)__popc(bal & ((1u << lane) - 1));
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const unsigned bal = __ballot_sync(0xffffffffu, use[j]);
-                    unsigned base = 0;
-                    if (lane == 0 && bal) base = atomicAdd(&S.nupd, (unsigned)__popc(bal));
-                    base = __shfl_sync(0xffffffffu, base, 0);
                     if (use[j]) {
                         const unsigned bin = (unsigned)(cell[j] >> a.coarse_shift);
-                        const unsigned at = base + __popc(bal & ((1u << lane) - 1));
+                        const unsigned at = base + (unsigned)j;
                         const uint32_t code =
                             ((uint32_t)(cell[j] & ((1ull << a.coarse_shift) - 1)) << 6) | slot[j];
                         if (PART == 2) {   // region beside the code
