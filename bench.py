@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -55,10 +56,16 @@ def describe(w: readsim.Workload) -> str:
 
 
 def source_sha() -> str:
+    """Hash of the insert kernels' code: the sources without comments and
+    blank lines, so that only a change of the code voids a DRAM record."""
     h = hashlib.sha256()
     for f in INSERT_SOURCES:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f) as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

@@ -1,34 +1,37 @@
 // Insertion phase of KmerCo (Algorithm 1 with the countBF insert of
 // Algorithm 3) on sm_103a.
 //
-// Work unit: a chunk of kChunk consecutive window starts of the flat bases
-// array, regardless of read boundaries, so long and short reads balance the
-// same way.  Per chunk a block
+// Work unit: a chunk of consecutive window starts of the flat bases array
+// (kChunk, or kPartChunk in the partitioned design), regardless of read
+// boundaries, so long and short reads balance the same way.  Per chunk a
+// block
 //   1. stages the chunk's bases (plus K-1 halo) in shared memory with
-//      16-byte streaming loads,
-//   2. packs them to 2-bit codes (A=0 C=1 G=2 T=3, first base most
-//      significant) with an invalid-base bitmap, and marks read starts in a
-//      break bitmap,
+//      16-byte streaming loads, and marks the read starts inside it in a
+//      break bitmap (no breaks when the reads are one sequence),
+//   2. packs the bases to 2-bit codes (A=0 C=1 G=2 T=3, first base most
+//      significant) with an invalid-base bitmap,
 //   3. keeps the window starts whose K bases are valid and lie in one read,
-//   4. per window: canonical key = min(forward, reverse complement)
-//      (Sections 2.2-2.3), k_h MurmurHash3 hashes, one saturating counter
-//      increment per hash by 64-bit compare-and-swap (Algorithm 3), and an
-//      insert into the distinct-key set (open addressing, linear probing);
-//      keys new to the set are staged in shared memory and appended to the
-//      distinct list with one global atomic per chunk.
+//   4. per window: the canonical key (the smaller of forward and reverse
+//      complement by value, or by H_0; Sections 2.2-2.3), k_h MurmurHash3
+//      hashes, one saturating counter increment per hash (Algorithm 3), and
+//      an insert into the distinct-key set (open addressing, linear
+//      probing); keys new to the set are staged in shared memory and
+//      appended to the distinct list with one global atomic per chunk.
 //
 // Two designs apply the counter increments of step 4:
 //  - atomic: each increment is a compare-and-swap on its 64-bit cell in
-//    global memory (any geometry);
-//  - partitioned (one-word keys, k_h <= 4, at most 2^26 cells): each
-//    increment is emitted as a 32-bit code; the chunk's codes are
-//    counting-sorted in shared memory into 64 coarse countBF regions and
-//    appended to per-region buffers with one cursor atomic per region and
-//    chunk.  repartition_kernel splits every coarse region into slices of
-//    2^14 cells (128 KiB), and apply_kernel loads one slice per block into
-//    shared memory, applies its increments there with shared-memory
-//    compare-and-swap and writes the slice back once.  Increments that do
-//    not fit a buffer fall back to the global compare-and-swap.
+//    global memory;
+//  - partitioned (k_h <= 4, at most 2^30 cells): each increment is emitted
+//    as a 32-bit code (cell within its coarse region, counter within the
+//    cell); the chunk's codes are counting-sorted in shared memory into 64
+//    coarse countBF regions and appended to per-region buffers with one
+//    cursor atomic per region and chunk.  repartition_kernel splits every
+//    region into slices, and one block per slice applies its increments in
+//    shared memory: apply_count_kernel (alpha <= 15) counts them in 32-bit
+//    lanes and adds the counts with saturation, apply_kernel uses
+//    shared-memory compare-and-swap on the cells.  Either writes the slice
+//    back once.  Increments that do not fit a buffer fall back to the global
+//    compare-and-swap.
 // Saturating increments commute, so both designs give the same countBF.
 #include "kmerco_internal.cuh"
 
