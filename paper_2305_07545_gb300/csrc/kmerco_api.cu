@@ -10,6 +10,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/kmerco.h"
 #include "kmerco_internal.cuh"
@@ -78,6 +79,12 @@ struct kmerco {
 };
 
 namespace {
+
+// NVTX range around one API call, so profilers show the phases by name.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 struct DeviceGuard {
     int prev = -1, want;
@@ -623,6 +630,7 @@ int kmerco_reset(kmerco_t *h) {
 }
 
 int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint64_t nreads) {
+    Range range("kmerco_insert");
     if (!h) return KMERCO_EINVAL;
     if (nreads == 0) return KMERCO_OK;
     if (!offsets || nreads >= 0xFFFFFFFFull) return KMERCO_EINVAL;
@@ -694,6 +702,7 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
 }
 
 int kmerco_classify(kmerco_t *h) {
+    Range range("kmerco_classify");
     if (!h) return KMERCO_EINVAL;
     if (h->classified) return KMERCO_OK;
     DeviceGuard guard(h->device);
@@ -969,6 +978,7 @@ int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est) {
 }
 
 int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
+    Range range("kmerco_merge");
     if (!dst || !src || dst == src) return KMERCO_EINVAL;
     if (dst->K != src->K || dst->G.m != src->G.m || dst->G.dim_x != src->G.dim_x ||
         dst->G.dim_y != src->G.dim_y || dst->alpha != src->alpha ||
@@ -1266,6 +1276,7 @@ void kmerco_batch_destroy(kmerco_batch_t *b) {
 
 int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
                         const uint64_t *const *offsets, const uint64_t *nreads, int reset) {
+    Range range("kmerco_batch_insert");
     if (!b || !bases || !offsets || !nreads) return KMERCO_EINVAL;
     DeviceGuard guard(b->device);
     // the same inputs as the captured launch: replay the graph
@@ -1426,6 +1437,7 @@ int kmerco_batch_schedule(kmerco_batch_t *b, int schedule, int streams) {
 }
 
 int kmerco_batch_classify(kmerco_batch_t *b) {
+    Range range("kmerco_batch_classify");
     if (!b) return KMERCO_EINVAL;
     DeviceGuard guard(b->device);
     // one readback of every sample's totals

@@ -27,7 +27,7 @@ import numpy as np
 from . import CountBF
 
 
-@dataclass
+@dataclass(eq=False)
 class Job:
     bases: object            # host uint8 array / pinned tensor of all reads
     offsets: object          # host uint64 offsets (nreads + 1)
@@ -81,9 +81,13 @@ class Server:
     """Continuous-batching service: `slots` jobs at most on the GPU at once,
     their estimated device memory at most `hbm_budget` bytes."""
 
-    def __init__(self, hbm_budget: int = 120 << 30, slots: int = 8):
+    def __init__(self, hbm_budget: int = 120 << 30, slots: int = 8, make_handle=None):
+        """``make_handle(job)`` creates a countBF handle for a job; by default
+        a :class:`CountBF` with the job's parameters."""
         self.budget = int(hbm_budget)
         self.slots = int(slots)
+        self._make = make_handle or (lambda job: CountBF(job.K, job.m, job.counter_bits,
+                                                         job.nhash, job.tau))
         self._cv = threading.Condition()
         self._pending: collections.deque = collections.deque()
         self._in_use = 0
@@ -136,7 +140,10 @@ class Server:
     # ------------------------------------------------------------- internal
     def _take_admissible(self):
         """First pending job that fits next to the running ones (caller holds
-        the lock).  Idle pooled handles are released to make room."""
+        the lock).  Idle pooled handles are released to make room; jobs
+        cancelled while waiting are dropped."""
+        if any(it[2].cancelled() for it in self._pending):
+            self._pending = collections.deque(it for it in self._pending if not it[2].cancelled())
         for idx, (job, need, fut, t_sub) in enumerate(self._pending):
             if self._in_use + need > self.budget:
                 continue
@@ -176,9 +183,18 @@ class Server:
                 if h is not None:
                     self._idle_bytes -= h._pool_bytes
             t_adm = self.now()
+            if not fut.set_running_or_notify_cancel():   # cancelled meanwhile
+                with self._cv:
+                    self._in_use -= need
+                    self._running -= 1
+                    if h is not None:
+                        self._pool[key].append(h)
+                        self._idle_bytes += h._pool_bytes
+                    self._cv.notify_all()
+                continue
             try:
                 if h is None:
-                    h = CountBF(job.K, job.m, job.counter_bits, job.nhash, job.tau)
+                    h = self._make(job)
                 res = self._run(job, h, t_sub, t_adm)
                 fut.set_result(res)
             except BaseException as e:   # the job fails, the server goes on

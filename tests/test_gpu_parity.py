@@ -449,3 +449,25 @@ def test_host_inputs_in_pieces_and_back_to_back_calls(update_mode):
     g = gpu_run(b, o, 27, 1 << 22, 4, 4, 2, update_mode=update_mode, device_inputs=False,
                 batches=[(b1, o1), (b2, o2)])
     check(g, b, o, 27, 4, 4, 2)
+
+
+def test_hbm_budget_is_enforced():
+    # the countBF alone is over the budget
+    with pytest.raises(kc.KmercoError) as e:
+        kc.CountBF(21, 1 << 30, 4, 3, 2, hbm_budget=1 << 20)
+    assert e.value.status == kc.ENOMEM
+    # the distinct set for this input is over the budget: the call fails
+    # before any device work and the handle stays usable
+    b, o = readsim.scaled("tiny", 2000, seed_offset=41).generate()
+    with kc.CountBF(21, 1 << 20, 4, 3, 2, hbm_budget=(1 << 19) + (1 << 20)) as bf:
+        with pytest.raises(kc.KmercoError) as e:
+            bf.insert(_dev(b), _dev(o))
+        assert e.value.status == kc.ENOMEM
+        bs, os_ = readsim.scaled("tiny", 40, seed_offset=42).generate()
+        bf.insert(_dev(bs), _dev(os_))
+        bf.classify()
+        keys, est = bf.distinct()
+        g = dict(stats=bf.stats(), counters=bf.counters(), keys=keys, est=est,
+                 trusted=bf.trusted(), erroneous=bf.erroneous())
+        assert g["stats"]["device_bytes"] <= (1 << 19) + (1 << 20)
+    check(g, bs, os_, 21, 4, 3, 2)
