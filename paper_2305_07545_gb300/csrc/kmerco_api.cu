@@ -722,7 +722,8 @@ int kmerco_classify(kmerco_t *h) {
     const uint64_t *sorted = distinct_in;
     const int bits = 2 * h->K;
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
-    if (kw == 1 && bits >= kHistBits + 8 && D > 1 &&
+    // (small sets: the radix sort, without the bucket sort's fixed scratch)
+    if (kw == 1 && bits >= kHistBits + 8 && D > 65536 &&
         D <= (uint64_t)kHistBins * (kBucketCap / 4)) {
         // Bucket sort: histogram of the top kHistBits key bits, adjacent bins
         // merged into super-buckets of at most kBucketCap keys, each sorted in
@@ -1044,6 +1045,13 @@ struct kmerco_batch {
     uint64_t buf_words[kBatchStreams][3];    // their sizes (coarse, fine, counters)
     std::vector<PartPlan> plans;             // per sample
     std::vector<uint64_t> load;              // per sample: windows, for stream assignment
+    // classification graph, replayed while the distinct counts and buffers match
+    bool have_cls;
+    cudaGraph_t cls_graph;
+    cudaGraphExec_t cls_exec;
+    std::vector<uint64_t> cls_key;           // D and buffer addresses of every sample
+    std::vector<const uint64_t *> cls_sorted;
+    uint64_t cls_launches;
 };
 
 namespace {
@@ -1253,6 +1261,10 @@ void kmerco_batch_destroy(kmerco_batch_t *b) {
         if (b->have_graph) {
             cudaGraphExecDestroy(b->exec);
             cudaGraphDestroy(b->graph);
+        }
+        if (b->have_cls) {
+            cudaGraphExecDestroy(b->cls_exec);
+            cudaGraphDestroy(b->cls_graph);
         }
         cudaFree(b->d_args);
         cudaFree(b->d_chunk_end);
@@ -1467,37 +1479,98 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
         return KMERCO_OK;
     }
     // every sample's radix sort, query and split, the samples spread over the
-    // streams by distinct count (no host synchronisation in between)
-    std::vector<int> order(b->n);
-    for (int i = 0; i < b->n; ++i) order[i] = i;
-    std::sort(order.begin(), order.end(), [&](int x, int y) { return D[x] > D[y]; });
-    std::vector<uint64_t> acc(kBatchStreams, 0);
-    KM_CUDA(cudaEventRecord(b->fork, b->stream));
-    for (int k = 0; k < kBatchStreams; ++k) KM_CUDA(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
-    for (int i : order) {
-        kmerco_t *h = b->h[i];
-        if (h->classified) continue;
-        int k = 0;
-        for (int j = 1; j < kBatchStreams; ++j)
-            if (acc[j] < acc[k]) k = j;
-        acc[k] += D[i] + 4096;
-        cudaStream_t st = b->aux[k];
-        const int bits = 2 * h->K, passes = (bits + kRadixBits - 1) / kRadixBits;
-        const uint64_t *sorted = h->dlist;
-        KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D[i], h->kw, bits, h->sort_scratch,
-                           &sorted, st));
-        KM_CUDA(launch_query(sorted, D[i], h->kw, h->K, h->G, h->est, st));
-        KM_CUDA(launch_split(sorted, h->est, D[i], h->kw, h->tau, h->split, h->split_scratch,
-                             h->ctr, st));
-        const uint64_t n_launch = (D[i] > 1 ? 3 * (uint64_t)passes : 0) + (D[i] ? 4 : 0);
-        h->launches += n_launch;
-        b->launches += n_launch;
-        h->sorted = sorted;
-        h->n_distinct = D[i];
+    // streams by distinct count (no host synchronisation in between), as one
+    // CUDA graph: replayed while every sample's distinct count and buffers
+    // are those it was captured with
+    std::vector<uint64_t> key;
+    key.reserve((size_t)b->n * 10);
+    for (int i = 0; i < b->n; ++i) {
+        const kmerco_t *h = b->h[i];
+        const uint64_t fields[10] = {h->classified ? ~0ull : D[i], (uint64_t)h->dlist,
+                                     (uint64_t)h->alt0, (uint64_t)h->alt1, (uint64_t)h->est,
+                                     (uint64_t)h->split, (uint64_t)h->sort_scratch,
+                                     (uint64_t)h->split_scratch, (uint64_t)h->ctr,
+                                     (uint64_t)h->G.cells};
+        key.insert(key.end(), fields, fields + 10);
     }
-    for (int k = 0; k < kBatchStreams; ++k) {
-        KM_CUDA(cudaEventRecord(b->join[k], b->aux[k]));
-        KM_CUDA(cudaStreamWaitEvent(b->stream, b->join[k], 0));
+    if (b->have_cls && key == b->cls_key) {
+        KM_CUDA(cudaGraphLaunch(b->cls_exec, b->stream));
+        b->launches += b->cls_launches;
+        for (int i = 0; i < b->n; ++i) {
+            kmerco_t *h = b->h[i];
+            if (h->classified) continue;
+            h->sorted = b->cls_sorted[i];
+            h->n_distinct = D[i];
+        }
+    } else {
+        if (b->have_cls) {
+            cudaGraphExecDestroy(b->cls_exec);
+            cudaGraphDestroy(b->cls_graph);
+            b->have_cls = false;
+        }
+        const bool capture =
+            cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (!capture) cudaGetLastError();   // plain launches on a stream that cannot capture
+        const uint64_t l0 = b->launches;
+        std::vector<int> order(b->n);
+        for (int i = 0; i < b->n; ++i) order[i] = i;
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return D[x] > D[y]; });
+        std::vector<uint64_t> acc(kBatchStreams, 0);
+        b->cls_sorted.assign(b->n, nullptr);
+        int st_launch = KMERCO_OK;
+        auto go = [&]() -> int {
+            KM_CUDA(cudaEventRecord(b->fork, b->stream));
+            for (int k = 0; k < kBatchStreams; ++k)
+                KM_CUDA(cudaStreamWaitEvent(b->aux[k], b->fork, 0));
+            for (int i : order) {
+                kmerco_t *h = b->h[i];
+                if (h->classified) continue;
+                int k = 0;
+                for (int j = 1; j < kBatchStreams; ++j)
+                    if (acc[j] < acc[k]) k = j;
+                acc[k] += D[i] + 4096;
+                cudaStream_t st = b->aux[k];
+                const int bits = 2 * h->K, passes = (bits + kRadixBits - 1) / kRadixBits;
+                const uint64_t *sorted = h->dlist;
+                KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D[i], h->kw, bits,
+                                   h->sort_scratch, &sorted, st));
+                KM_CUDA(launch_query(sorted, D[i], h->kw, h->K, h->G, h->est, st));
+                KM_CUDA(launch_split(sorted, h->est, D[i], h->kw, h->tau, h->split,
+                                     h->split_scratch, h->ctr, st));
+                const uint64_t n_launch = (D[i] > 1 ? 3 * (uint64_t)passes : 0) + (D[i] ? 4 : 0);
+                h->launches += n_launch;
+                b->launches += n_launch;
+                h->sorted = sorted;
+                h->n_distinct = D[i];
+                b->cls_sorted[i] = sorted;
+            }
+            for (int k = 0; k < kBatchStreams; ++k) {
+                KM_CUDA(cudaEventRecord(b->join[k], b->aux[k]));
+                KM_CUDA(cudaStreamWaitEvent(b->stream, b->join[k], 0));
+            }
+            return KMERCO_OK;
+        };
+        st_launch = go();
+        if (capture) {
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+            if (st_launch != KMERCO_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st_launch;
+            }
+            KM_CUDA(ec);
+            if (cudaGraphInstantiate(&b->cls_exec, g, 0) != cudaSuccess) {
+                cudaGraphDestroy(g);
+                return KMERCO_ECUDA;
+            }
+            b->cls_graph = g;
+            b->have_cls = true;
+            b->cls_key = key;
+            b->cls_launches = b->launches - l0;
+            KM_CUDA(cudaGraphLaunch(b->cls_exec, b->stream));
+        } else if (st_launch != KMERCO_OK) {
+            return st_launch;
+        }
     }
     // one readback of every sample's trustworthy count
     for (kmerco_t *h : b->h)

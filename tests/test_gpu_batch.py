@@ -134,3 +134,28 @@ def test_batch_rejects_bad_arguments():
     assert e.value.status == kc.EINVAL
     for f in (a, b, c):
         f.close()
+
+
+def test_batch_classify_graph_replay():
+    # the second classification of the same input replays the captured graph
+    samples = _samples()[2:8]
+    stream = torch.cuda.Stream()
+    filters = [kc.CountBF(25, m, alpha, nhash, tau, stream=stream.cuda_stream)
+               for (_, _, m, alpha, nhash, tau) in samples]
+    dev = [(_dev(b), _dev(o)) for (b, o, *_rest) in samples]
+    torch.cuda.synchronize()
+    nreads = [len(o) - 1 for (_, o, *_r) in samples]
+    with kc.Batch(filters) as batch:
+        for rep in range(3):
+            kc.kmerco_batch_insert(batch.b, [d[0] if n else None for d, n in zip(dev, nreads)],
+                                   [d[1] for d in dev], nreads, reset=True)
+            l0 = batch.info()["launches"]
+            batch.classify()
+            assert batch.info()["launches"] > l0
+            for (b, o, m, alpha, nhash, tau), f in zip(samples, filters):
+                keys, est = f.distinct()
+                g = dict(stats=f.stats(), counters=f.counters(), keys=keys, est=est,
+                         trusted=f.trusted(), erroneous=f.erroneous())
+                check(g, b, o, 25, alpha, nhash, tau)
+    for f in filters:
+        f.close()
