@@ -165,11 +165,18 @@ def cpu_oracle_rate(bases, offsets, w, n_reads: int) -> dict:
     dhi, dlo, _ = oracle.distinct(ex.hi, ex.lo)
     oracle.classify(filt, dhi, dlo, w.K, w.m, w.alpha, w.nhash, w.tau)
     dt = time.perf_counter() - t0
+    # untimed: Algorithm 1's sequential first-seen count (query 0 before the
+    # insert) against the exact distinct count, on the first 2e6 K-mers
+    n2 = min(ex.n, 2_000_000)
+    first_seen = oracle.seq_distinct(ex.hi[:n2], ex.lo[:n2], w.K, w.m, w.alpha, w.nhash)
+    exact = len(oracle.distinct(ex.hi[:n2], ex.lo[:n2])[1])
     return {"value": ex.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "seconds": round(dt, 3),
             "sample": f"first {n_reads:,} reads of the workload ({ex.n:,} K-mers): oracle "
                       f"extraction + sequential Algorithm 3 + sort/unique + Algorithm 2, "
-                      f"single-threaded C on the host"}
+                      f"single-threaded C on the host",
+            "distinct_first_K_mers": {"kmers": n2, "exact": exact,
+                                      "sequential_first_seen": first_seen}}
 
 
 def dist_setup():
