@@ -356,7 +356,8 @@ def run_ours(args) -> None:
     launch_bytes = bases.nbytes + offsets.nbytes + inserted * kmer_bytes + distinct * 16
     avg_insert_ms = statistics.mean(insert_ms)
     achieved = launch_bytes / (avg_insert_ms / 1000.0) / 1e9
-    traffic = recorded_traffic()
+    # the ncu record covers the full `single` call only
+    traffic = recorded_traffic() if args.workload == "single" and not args.reads else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "insert phase: every kernel of one kmerco_insert call (insert_kernel: "

@@ -244,6 +244,8 @@ int kmerco_merge(kmerco_t *dst, kmerco_t *src);
  * cells, keys (n keys of 1 word for k <= 32, 2 words low-first otherwise),
  * est (n uint32) and out (n keys) are device memory on the current device.
  * m must be a multiple of floor(64 / counter_bits), e.g. stats.m_actual.
+ * The countBF is the flat one (addressing g = h mod m); a two-dimensional
+ * countBF (kmerco_config_t.dim_x) is classified through its handle instead.
  *
  * Nothing is allocated.  The only scratch is one fixed device array of
  * KMERCO_NOALLOC_MAX_KEYS / 4096 + 1 uint64 (512 KiB + 8 bytes) that every
