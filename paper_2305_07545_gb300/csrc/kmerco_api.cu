@@ -345,22 +345,49 @@ InsertArgs sample_args(const kmerco_t *h, const uint8_t *d_bases, const uint64_t
     return a;
 }
 
-// A host input copied to the device in pieces on its own stream, each piece
-// inserted as soon as it (and the K - 1 bytes after it) has arrived.
+// A host input copied to the device on its own stream in npieces equal byte
+// pieces, each with an event; an insert launch waits only for the pieces
+// holding its bytes (its chunks and the K - 1 bytes after them).
 struct HostCopy {
-    const uint8_t *src;          // host bytes of the call (from offsets[0])
-    uint8_t *dst;                // device staging of the same bytes
-    cudaStream_t stream;
-    cudaEvent_t *ev;             // kCopyPieces + 1 events
-    cudaEvent_t fork;
+    uint64_t nbytes;
+    int npieces;
+    cudaEvent_t *ev;             // one per piece
+    uint64_t piece_lo(int i) const { return nbytes * (uint64_t)i / (uint64_t)npieces; }
 };
+
+// Issue the copy of nbytes host bytes src -> dst in pieces on the handle's
+// copy stream, after the work already queued on the handle's stream (the
+// previous call may still read dst).
+int issue_host_copy(kmerco_t *h, const uint8_t *src, uint8_t *dst, uint64_t nbytes,
+                    HostCopy &hc) {
+    if (!h->copy_stream) {
+        bool ok = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&h->copy_fork, cudaEventDisableTiming) == cudaSuccess;
+        for (int i = 0; ok && i <= kCopyPieces; ++i)
+            ok = cudaEventCreateWithFlags(&h->copy_ev[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return KMERCO_ECUDA;
+    }
+    hc.nbytes = nbytes;
+    hc.npieces = nbytes >= (8ull << 20) ? kCopyPieces : 1;
+    hc.ev = h->copy_ev;
+    KM_CUDA(cudaEventRecord(h->copy_fork, h->stream));
+    KM_CUDA(cudaStreamWaitEvent(h->copy_stream, h->copy_fork, 0));
+    for (int i = 0; i < hc.npieces; ++i) {
+        const uint64_t lo = hc.piece_lo(i), hi = hc.piece_lo(i + 1);
+        if (hi > lo)
+            KM_CUDA(cudaMemcpyAsync(dst + lo, src + lo, hi - lo, cudaMemcpyHostToDevice,
+                                    h->copy_stream));
+        KM_CUDA(cudaEventRecord(h->copy_ev[i], h->copy_stream));
+    }
+    return KMERCO_OK;
+}
 
 // All device work of one insert call on stream s, without host
 // synchronisation (so it can be captured): first reads of the chunks, then
 // per pass the insert kernel and, in the partitioned design, repartition and
 // apply.  h->first_read must hold the call's chunks; pb holds pp's buffers.
-// With hc, the call's bytes are copied from the host in up to kCopyPieces
-// chunk ranges, overlapped with the insert launches of the earlier ranges.
+// With hc (a host input being copied), each pass is split into up to
+// kCopyPieces launches, each waiting only for the pieces it reads.
 int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
                          const PartBufs &pb, cudaStream_t s, uint64_t &launches,
                          const HostCopy *hc = nullptr) {
@@ -378,26 +405,6 @@ int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
     }
     cut.push_back(nchunks);
     const uint64_t nr = cut.size() - 1;
-    const bool piecewise = hc && nr <= (uint64_t)kCopyPieces;
-    if (hc) {
-        // the staging buffer may still be read by the previous call's kernels
-        KM_CUDA(cudaEventRecord(hc->fork, s));
-        KM_CUDA(cudaStreamWaitEvent(hc->stream, hc->fork, 0));
-        if (piecewise) {
-            for (uint64_t r = 0; r < nr; ++r) {
-                const uint64_t lo = std::min(cut[r] * chunk, nbytes);
-                const uint64_t hi = r + 1 == nr ? nbytes : std::min(cut[r + 1] * chunk, nbytes);
-                if (hi > lo)
-                    KM_CUDA(cudaMemcpyAsync(hc->dst + lo, hc->src + lo, hi - lo,
-                                            cudaMemcpyHostToDevice, hc->stream));
-                KM_CUDA(cudaEventRecord(hc->ev[r], hc->stream));
-            }
-        } else {
-            KM_CUDA(cudaMemcpyAsync(hc->dst, hc->src, nbytes, cudaMemcpyHostToDevice, hc->stream));
-            KM_CUDA(cudaEventRecord(hc->ev[0], hc->stream));
-            KM_CUDA(cudaStreamWaitEvent(s, hc->ev[0], 0));
-        }
-    }
     KM_CUDA(launch_first_read(a.offsets, a.nreads, a.first, nchunks, chunk, h->first_read, s));
     launches += nchunks ? 1 : 0;
     a.part = pp.part ? 1 : 0;
@@ -413,9 +420,12 @@ int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
         const uint64_t pass_end = nchunks * (pass + 1) / pp.passes;
         if (pp.part) KM_CUDA(cudaMemsetAsync(pb.ctr, 0, pp.ctr_words() * 8, s));
         for (; r < nr && cut[r + 1] <= pass_end && cut[r] < pass_end; ++r) {
-            if (piecewise) {   // this range's bytes and the K - 1 after it
-                KM_CUDA(cudaStreamWaitEvent(s, hc->ev[r], 0));
-                if (r + 1 < nr) KM_CUDA(cudaStreamWaitEvent(s, hc->ev[r + 1], 0));
+            if (hc) {   // the pieces holding this range's bytes and the K - 1 after it
+                const uint64_t lo = cut[r] * chunk;
+                const uint64_t hi = std::min(cut[r + 1] * chunk + (uint64_t)a.K - 1, nbytes);
+                for (int i = 0; i < hc->npieces; ++i)
+                    if (hc->piece_lo(i) < hi && hc->piece_lo(i + 1) > lo)
+                        KM_CUDA(cudaStreamWaitEvent(s, hc->ev[i], 0));
             }
             a.chunk_begin = cut[r];
             a.nchunks = cut[r + 1];
@@ -638,7 +648,18 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     const int K = h->K;
     uint64_t first, last, bound = 0;
     const uint64_t *d_off = offsets;
-    if (!is_device_ptr(offsets)) {   // host offsets: checked and summed on the device too
+    const bool host_offsets = !is_device_ptr(offsets);
+    const bool host_bases = bases && !is_device_ptr(bases);
+    HostCopy hc;
+    bool copying = false;
+    if (host_offsets) {   // checked and summed on the device too
+        if (host_bases && offsets[nreads] > offsets[0]) {
+            // the reads' bytes start moving now, while the offsets are checked
+            const uint64_t nb = offsets[nreads] - offsets[0];
+            KM_TRY(ensure(h, &h->in_bases, &h->in_bases_cap, nb));
+            KM_TRY(issue_host_copy(h, (const uint8_t *)bases + offsets[0], h->in_bases, nb, hc));
+            copying = true;
+        }
         KM_TRY(ensure(h, &h->in_offsets, &h->in_offsets_cap, nreads + 1));
         KM_CUDA(cudaMemcpyAsync(h->in_offsets, offsets, (nreads + 1) * 8, cudaMemcpyHostToDevice,
                                 h->stream));
@@ -658,14 +679,16 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     const uint64_t nbytes = last - first;
     if (nbytes && !bases) return KMERCO_EINVAL;
     const uint8_t *d_bases = nullptr;
-    bool host_bases = false;
     if (nbytes) {
-        if (is_device_ptr(bases)) {
+        if (!host_bases) {
             d_bases = (const uint8_t *)bases + first;
-        } else {   // copied below, piece by piece, while the insert runs
-            KM_TRY(ensure(h, &h->in_bases, &h->in_bases_cap, nbytes));
+        } else {   // copied piece by piece on the copy stream (issued above when it could be)
+            if (!copying) {
+                KM_TRY(ensure(h, &h->in_bases, &h->in_bases_cap, nbytes));
+                KM_TRY(issue_host_copy(h, (const uint8_t *)bases + first, h->in_bases, nbytes, hc));
+                copying = true;
+            }
             d_bases = h->in_bases;
-            host_bases = true;
         }
     }
     if (bound == 0) return KMERCO_OK;   // no window fits in any read
@@ -680,21 +703,9 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     const uint64_t chunk = pp.part ? kPartChunk : kChunk;
     KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, (nbytes + chunk - 1) / chunk));
     const InsertArgs a = sample_args(h, d_bases, d_off, nreads, first, last);
-    HostCopy hc;
-    if (host_bases) {
-        if (!h->copy_stream) {
-            bool ok = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) == cudaSuccess &&
-                      cudaEventCreateWithFlags(&h->copy_fork, cudaEventDisableTiming) == cudaSuccess;
-            for (int i = 0; ok && i <= kCopyPieces; ++i)
-                ok = cudaEventCreateWithFlags(&h->copy_ev[i], cudaEventDisableTiming) == cudaSuccess;
-            if (!ok) return KMERCO_ECUDA;
-        }
-        hc = HostCopy{(const uint8_t *)bases + first, h->in_bases, h->copy_stream, h->copy_ev,
-                      h->copy_fork};
-    }
     KM_CUDA(cudaEventRecord(h->ev[0], h->stream));
     KM_TRY(launch_sample_insert(h, a, pp, PartBufs{h->coarse, h->fine, h->part_ctr}, h->stream,
-                                h->launches, host_bases ? &hc : nullptr));
+                                h->launches, copying ? &hc : nullptr));
     KM_CUDA(cudaEventRecord(h->ev[1], h->stream));
     h->insert_timed = true;
     h->classified = false;
