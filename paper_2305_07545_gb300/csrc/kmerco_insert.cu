@@ -42,12 +42,10 @@ namespace {
 template <int CHUNK>
 struct ChunkDims {
     static constexpr int kPack32 = CHUNK / 16 + 8;   // 16 bases per 32-bit word; chunk + 128 bases
-    static constexpr int kRaw = kPack32 * 16 + 32;   // >= CHUNK + 63 bases + alignment slack
 };
 
 template <int KW, int CHUNK, int PART>
 struct __align__(16) InsertSmem {
-    uint8_t raw[ChunkDims<CHUNK>::kRaw];        // raw[head + q] = base q of the chunk
     uint32_t pk[ChunkDims<CHUNK>::kPack32];     // codes; word t at t ^ 1 so pairs read as u64
     uint16_t inv[ChunkDims<CHUNK>::kPack32];    // bit j of inv[t]: base 16t + j is not ACGTacgt
     uint32_t brk[ChunkDims<CHUNK>::kPack32 / 2];  // bit q: a read starts at base q of the chunk
@@ -186,20 +184,8 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
     const unsigned head = (unsigned)(src & 15);
     const uintptr_t abase = src - head;
 
-    // 1. stage bytes [c0, e) at raw[head ...]: whole 16-byte vectors
-    //    inside the range with streaming loads, partial ones bytewise.
-    const unsigned nvec = (head + nb + 15) >> 4;
-    for (unsigned v = tid; v < nvec; v += kInsertThreads) {
-        unsigned lo = v << 4, hi = lo + 16;
-        if (lo >= head && hi <= head + nb) {
-            *(uint4 *)(S.raw + lo) = __ldcs((const uint4 *)(abase + lo));
-        } else {
-            for (unsigned b = lo; b < hi; ++b)
-                if (b >= head && b < head + nb) S.raw[b] = *(const uint8_t *)(abase + b);
-        }
-    }
-    // read starts inside the staged span (none when the reads are one
-    // sequence), loaded alongside the bytes; S.brk is zero on entry
+    // 1. read starts inside the chunk's span (none when the reads are one
+    //    sequence); S.brk is zero on entry
     for (uint64_t r = (uint64_t)a.first_read[chunk] + tid; !a.whole_file && r < a.nreads;
          r += kInsertThreads) {
         uint64_t s = a.offsets[r] - a.first;
@@ -217,18 +203,64 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
         S.hist[tid] = 0;
         S.fill[tid] = 0;
     }
-    __syncthreads();
-
-    // 2a. pack: 16 bases per thread -> 2-bit codes + invalid bits
+    // 2. bases [16t, 16t + 16) of the span straight from global memory (the
+    //    two 16-byte vectors holding them: whole ones with streaming loads,
+    //    the partial ones at the span's ends bytewise, 'N' outside it), then
+    //    2-bit codes + invalid bits
     for (int t = tid; t < kPack32; t += kInsertThreads) {
+        uint32_t w[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const unsigned lo = (unsigned)(t + h) << 4;
+            if (lo >= head && lo + 16 <= head + nb) {
+                const uint4 v = __ldcs((const uint4 *)(abase + lo));
+                w[4 * h] = v.x;
+                w[4 * h + 1] = v.y;
+                w[4 * h + 2] = v.z;
+                w[4 * h + 3] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const unsigned b = lo + 4 * q + k;
+                        const unsigned c = b >= head && b < head + nb
+                                               ? *(const uint8_t *)(abase + b) : (unsigned)'N';
+                        word |= c << (8 * k);
+                    }
+                    w[4 * h + q] = word;
+                }
+            }
+        }
+        // the 16 bytes start `head` bytes into the 32 loaded ones
+        const unsigned hb = (head & 3) * 8;
+        uint32_t x[4];
+        switch (head >> 2) {
+        case 0:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = __funnelshift_r(w[i], w[i + 1], hb);
+            break;
+        case 1:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = __funnelshift_r(w[i + 1], w[i + 2], hb);
+            break;
+        case 2:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = __funnelshift_r(w[i + 2], w[i + 3], hb);
+            break;
+        default:
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = __funnelshift_r(w[i + 3], w[i + 4], hb);
+            break;
+        }
         uint32_t code = 0, bad = 0;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            unsigned q = (unsigned)t * 16 + j;
-            unsigned c = q < nb ? S.raw[head + q] : 'N';
-            unsigned u = c | 0x20u;
-            bool ok = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
-            unsigned cd = ((c >> 1) ^ (c >> 2)) & 3u;   // A,a->0 C,c->1 G,g->2 T,t->3
+            const unsigned c = (x[j >> 2] >> (8 * (j & 3))) & 0xFFu;
+            const unsigned u = c | 0x20u;
+            const bool ok = (u == 'a') | (u == 'c') | (u == 'g') | (u == 't');
+            const unsigned cd = ((c >> 1) ^ (c >> 2)) & 3u;   // A,a->0 C,c->1 G,g->2 T,t->3
             code = (code << 2) | (ok ? cd : 0u);
             bad |= (ok ? 0u : 1u) << j;
         }
