@@ -437,18 +437,82 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(const uint64_t *key
     }
 }
 
+// The same placement with the tile's keys first grouped by super-bucket in
+// shared memory, so that each super-bucket's keys of the tile leave as one
+// contiguous run (coalesced stores).  For at most kSortedScatterMax
+// super-buckets; the tile is kSortedScatterTile keys, 1,024 threads.
+constexpr int kSortedScatterTile = 16384;
+constexpr int kSortedScatterMax = 4096;
+
+__global__ void __launch_bounds__(1024) bucket_scatter_sorted_kernel(
+    const uint64_t *keys, uint64_t n, int shift, const unsigned *map, unsigned nsuper,
+    unsigned long long *cursor, uint64_t *out) {
+    extern __shared__ unsigned long long ss[];
+    uint64_t *tile = (uint64_t *)ss;
+    unsigned *h = (unsigned *)(ss + kSortedScatterTile);
+    unsigned *lst = h + nsuper, *fill = lst + nsuper, *base = fill + nsuper;
+    constexpr unsigned kT = 1024, kPer = kSortedScatterTile / kT;
+    const uint64_t t0 = (uint64_t)blockIdx.x * kSortedScatterTile;
+    const unsigned cnt = (unsigned)min((uint64_t)kSortedScatterTile, n - t0);
+    const unsigned tid = threadIdx.x;
+    for (unsigned i = tid; i < nsuper; i += kT) {
+        h[i] = 0;
+        fill[i] = 0;
+    }
+    __syncthreads();
+    uint64_t k[kPer];
+    unsigned bk[kPer];
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q) {
+        const unsigned i = q * kT + tid;
+        k[q] = i < cnt ? __ldg(keys + t0 + i) : 0;
+    }
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q) {
+        bk[q] = __ldg(map + (k[q] >> shift));
+        if (q * kT + tid < cnt) atomicAdd(&h[bk[q]], 1u);
+    }
+    __syncthreads();
+    // tile-local starts (exclusive scan of h, a run of entries per thread)
+    // and one global reservation per super-bucket present in the tile
+    {
+        const unsigned per = (nsuper + kT - 1) / kT, b0 = tid * per;
+        unsigned sum = 0;
+        for (unsigned j = 0; j < per && b0 + j < nsuper; ++j) sum += h[b0 + j];
+        unsigned tot;
+        unsigned pre = block_exclusive_scan_n<unsigned, kT>(sum, tot);
+        for (unsigned j = 0; j < per && b0 + j < nsuper; ++j) {
+            const unsigned b = b0 + j, m = h[b];
+            lst[b] = pre;
+            pre += m;
+            if (m) base[b] = (unsigned)atomicAdd(cursor + b, (unsigned long long)m);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q)
+        if (q * kT + tid < cnt) tile[lst[bk[q]] + atomicAdd(&fill[bk[q]], 1u)] = k[q];
+    __syncthreads();
+    for (unsigned i = tid; i < cnt; i += kT) {
+        const uint64_t key = tile[i];
+        const unsigned b = __ldg(map + (key >> shift));
+        out[base[b] + (i - lst[b])] = key;
+    }
+}
+
 // Sort of one super-bucket (at most kBucketCap keys) in shared memory: a
 // counting sort on the 12 bits below the super-bucket's common range
 // (sub = (key - lo) >> rsh), then an insertion sort of each small
 // sub-bucket.  When the keys cluster so that a sub-bucket holds more than
 // kSubMax keys, the block bitonic-sorts the whole super-bucket instead.
-__global__ void __launch_bounds__(kBucketThreads) bucket_sort_kernel(
+__global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort_kernel(
     uint64_t *data, const unsigned long long *start, const unsigned long long *lo,
     const int *rsh) {
     extern __shared__ unsigned long long sm[];
-    unsigned long long *A = sm, *B = sm + kBucketCap;
-    unsigned *hist = (unsigned *)(sm + 2 * kBucketCap);
+    unsigned long long *B = sm;   // the keys stay in registers until placed here
+    unsigned *hist = (unsigned *)(sm + kBucketCap);
     unsigned *st = hist + kSubBins, *fill = st + kSubBins;
+    constexpr unsigned kPer = kBucketCap / kBucketThreads;
     __shared__ unsigned maxsub;
     const unsigned long long s0 = start[blockIdx.x];
     const unsigned n = (unsigned)(start[blockIdx.x + 1] - s0);
@@ -459,10 +523,12 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_sort_kernel(
     for (unsigned i = tid; i < kSubBins; i += kBucketThreads) hist[i] = 0;
     if (tid == 0) maxsub = 0;
     __syncthreads();
-    for (unsigned i = tid; i < n; i += kBucketThreads) {
-        const unsigned long long k = data[s0 + i];
-        A[i] = k;
-        atomicAdd(&hist[min((unsigned)((k - base) >> r), (unsigned)kSubBins - 1)], 1u);
+    unsigned long long key[kPer];
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q) {
+        const unsigned i = q * kBucketThreads + tid;
+        key[q] = i < n ? data[s0 + i] : 0ull;
+        if (i < n) atomicAdd(&hist[min((unsigned)((key[q] - base) >> r), (unsigned)kSubBins - 1)], 1u);
     }
     __syncthreads();
     // exclusive scan of the kSubBins counts: 4 per thread
@@ -485,9 +551,12 @@ __global__ void __launch_bounds__(kBucketThreads) bucket_sort_kernel(
         atomicMax(&maxsub, mx);
     }
     __syncthreads();
-    for (unsigned i = tid; i < n; i += kBucketThreads) {
-        const unsigned long long k = A[i];
-        B[atomicAdd(&fill[min((unsigned)((k - base) >> r), (unsigned)kSubBins - 1)], 1u)] = k;
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q) {
+        if (q * kBucketThreads + tid < n) {
+            const unsigned long long k = key[q];
+            B[atomicAdd(&fill[min((unsigned)((k - base) >> r), (unsigned)kSubBins - 1)], 1u)] = k;
+        }
     }
     __syncthreads();
     if (maxsub <= (unsigned)kSubMax) {
@@ -562,12 +631,22 @@ cudaError_t bucket_place_and_sort(const uint64_t *in, uint64_t *out, uint64_t n,
     cudaError_t e = cudaMemcpyAsync(cursor, start, nsuper * sizeof(unsigned long long),
                                     cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
-    const int smem = (int)(2 * nsuper * sizeof(unsigned));
-    e = cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    bucket_scatter_kernel<<<(unsigned)((n + kScatterTile - 1) / kScatterTile), 256, smem, s>>>(
-        in, n, shift, map, nsuper, cursor, out);
-    const int ssmem = 2 * kBucketCap * 8 + 3 * kSubBins * 4;
+    if (nsuper <= (unsigned)kSortedScatterMax) {
+        const int smem = (int)(kSortedScatterTile * sizeof(uint64_t) + 4 * nsuper * sizeof(unsigned));
+        e = cudaFuncSetAttribute(bucket_scatter_sorted_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        bucket_scatter_sorted_kernel<<<(unsigned)((n + kSortedScatterTile - 1) / kSortedScatterTile),
+                                       1024, smem, s>>>(in, n, shift, map, nsuper, cursor, out);
+    } else {
+        const int smem = (int)(2 * nsuper * sizeof(unsigned));
+        e = cudaFuncSetAttribute(bucket_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+        if (e != cudaSuccess) return e;
+        bucket_scatter_kernel<<<(unsigned)((n + kScatterTile - 1) / kScatterTile), 256, smem, s>>>(
+            in, n, shift, map, nsuper, cursor, out);
+    }
+    const int ssmem = kBucketCap * 8 + 3 * kSubBins * 4;
     e = cudaFuncSetAttribute(bucket_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem);
     if (e != cudaSuccess) return e;
     bucket_sort_kernel<<<nsuper, kBucketThreads, ssmem, s>>>(out, start, lo, rsh);
