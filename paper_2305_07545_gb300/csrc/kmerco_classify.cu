@@ -271,13 +271,17 @@ __global__ void query_kernel(const uint64_t *keys, uint64_t n, int K, Geometry G
     }
 }
 
-// Trusted keys per split tile (each thread owns 16 consecutive keys).
+// Trusted keys per split tile.  A tile of kSplitTile keys is read in 16
+// rounds of kSortThreads consecutive keys (coalesced), key tile0 + 256j + tid.
 __global__ void __launch_bounds__(kSortThreads) split_count_kernel(const uint32_t *est, uint64_t n,
                                                                    uint32_t tau, uint64_t *tile_cnt) {
-    const uint64_t base = (uint64_t)blockIdx.x * kSplitTile + threadIdx.x * 16ull;
+    const uint64_t tile0 = (uint64_t)blockIdx.x * kSplitTile;
     unsigned c = 0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) c += (base + j < n) && est[base + j] > tau;
+    for (int j = 0; j < kSplitTile / kSortThreads; ++j) {
+        const uint64_t i = tile0 + (uint64_t)j * kSortThreads + threadIdx.x;
+        c += (i < n) && est[i] > tau;
+    }
     unsigned long long tot;
     block_exclusive_scan<unsigned long long>(c, tot);
     if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
@@ -297,6 +301,11 @@ __global__ void __launch_bounds__(kSortThreads) split_scan_kernel(uint64_t *tile
     if (threadIdx.x == 0) ctr->trusted = carry;
 }
 
+// Stable split of one tile: trustworthy keys (est > tau) go after the
+// trustworthy keys of earlier tiles, erroneous keys after all trustworthy
+// keys and the erroneous keys of earlier tiles, both in key order.  The tile
+// is read in 16 coalesced rounds; a key's rank comes from its warp's ballot
+// and the counts of the (round, warp) segments before it.
 template <int KW>
 __global__ void __launch_bounds__(kSortThreads) split_scatter_kernel(const uint64_t *keys,
                                                                      const uint32_t *est, uint64_t n,
@@ -304,26 +313,38 @@ __global__ void __launch_bounds__(kSortThreads) split_scatter_kernel(const uint6
                                                                      const uint64_t *tile_pre,
                                                                      const DevCounters *ctr,
                                                                      uint64_t *out) {
+    constexpr int kRounds = kSplitTile / kSortThreads;
+    __shared__ unsigned seg[kRounds * kWarps];   // trusted keys per (round, warp), then their prefix
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t tile0 = (uint64_t)blockIdx.x * kSplitTile;
-    const uint64_t base = tile0 + threadIdx.x * 16ull;
-    unsigned flags = 0, c = 0;
+    unsigned bal[kRounds];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        bool t = (base + j < n) && est[base + j] > tau;
-        flags |= (unsigned)t << j;
-        c += t;
+    for (int j = 0; j < kRounds; ++j) {
+        const uint64_t i = tile0 + (uint64_t)j * kSortThreads + threadIdx.x;
+        bal[j] = __ballot_sync(0xffffffffu, i < n && est[i] > tau);
+        if (lane == 0) seg[j * kWarps + warp] = __popc(bal[j]);
     }
-    unsigned long long tot;
-    const unsigned long long pre = block_exclusive_scan<unsigned long long>(c, tot);
+    __syncthreads();
+    if (threadIdx.x == 0) {   // segments in key order: round-major, then warp
+        unsigned acc = 0;
+        for (int q = 0; q < kRounds * kWarps; ++q) {
+            const unsigned v = seg[q];
+            seg[q] = acc;
+            acc += v;
+        }
+    }
+    __syncthreads();
     const uint64_t T = ctr->trusted;
-    uint64_t tpos = tile_pre[blockIdx.x] + pre;
-    const uint64_t before = base < n ? base - tile0 : (n > tile0 ? n - tile0 : 0);
-    uint64_t epos = T + (tile0 - tile_pre[blockIdx.x]) + (before - pre);
+    const uint64_t tpre = tile_pre[blockIdx.x];   // trusted keys before this tile
+    const unsigned lt = (1u << lane) - 1;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const uint64_t i = base + j;
-        if (i >= n) break;
-        const uint64_t o = (flags >> j) & 1u ? tpos++ : epos++;
+    for (int j = 0; j < kRounds; ++j) {
+        const uint64_t i = tile0 + (uint64_t)j * kSortThreads + threadIdx.x;
+        if (i >= n) continue;
+        const uint64_t off = i - tile0;   // keys of the tile before this one
+        const uint64_t tr_before = seg[j * kWarps + warp] + __popc(bal[j] & lt);
+        const uint64_t o = (bal[j] >> lane) & 1u ? tpre + tr_before
+                                                : T + (tile0 - tpre) + (off - tr_before);
 #pragma unroll
         for (int w = 0; w < KW; ++w) out[o * KW + w] = keys[i * KW + w];
     }
