@@ -282,7 +282,11 @@ struct PartPlan {
     int coarse_shift = 0, slice_shift = 0;
     uint64_t coarse_cap = 0, fine_cap = 0, nslices = 0, passes = 1;
     uint64_t coarse_words() const { return kCoarseBins * coarse_cap; }   // uint32 codes
-    uint64_t fine_words() const { return repart ? nslices * fine_cap : 0; }
+    // slice codes: uint16 counting lanes (two per 32-bit word) or uint32 codes
+    bool lane_codes() const { return repart && count; }
+    uint64_t fine_words() const {
+        return !repart ? 0 : lane_codes() ? (nslices * fine_cap + 1) / 2 : nslices * fine_cap;
+    }
     uint64_t ctr_words() const { return 2 * kCoarseBins + 2 * nslices; }
 };
 
@@ -318,7 +322,7 @@ PartPlan plan_partition(const kmerco_t *h, uint64_t bound, uint64_t nbytes) {
     pp.coarse_cap = Up / kCoarseBins;
     pp.coarse_cap = (pp.coarse_cap + pp.coarse_cap / 6 + 4096 + 3) & ~3ull;   // multiple of 4
     pp.fine_cap = pp.repart ? Up / pp.nslices : 0;
-    pp.fine_cap = (pp.fine_cap + pp.fine_cap / 5 + 1024 + 3) & ~3ull;
+    pp.fine_cap = (pp.fine_cap + pp.fine_cap / 5 + 1024 + 7) & ~7ull;   // multiple of 8
     return pp;
 }
 
@@ -445,6 +449,7 @@ int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
             p.coarse_written = a.coarse_written;
             p.fine = pb.fine;
             p.fine_cap = pp.fine_cap;
+            p.lane_codes = pp.lane_codes() ? 1 : 0;
             p.fine_cursor = fine_cursor;
             p.fine_written = fine_written;
             p.ctr = h->ctr;
@@ -456,6 +461,7 @@ int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
         ap.slice_shift = pp.slice_shift;
         ap.codes = pp.repart ? pb.fine : pb.coarse;
         ap.cap = pp.repart ? pp.fine_cap : pp.coarse_cap;
+        ap.lane_codes = pp.lane_codes() ? 1 : 0;
         ap.written = pp.repart ? fine_written : a.coarse_written;
         ap.ctr = h->ctr;
         KM_CUDA(pp.count ? launch_apply_count(ap, pp.nslices, s) : launch_apply(ap, pp.nslices, s));

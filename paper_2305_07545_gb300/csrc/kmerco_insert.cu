@@ -754,10 +754,12 @@ __device__ __forceinline__ void repart_scan(const unsigned *v, unsigned *out, un
     if (2 * tid + 1 < n) out[2 * tid + 1] = off + v0;
 }
 
-// Split each coarse region's increment codes into slices of 2^kSliceShift
+// Split each coarse region's increment codes into slices of 2^slice_shift
 // cells.  Block (x, y) takes tile x of coarse region y.  MAXF bounds the
-// slices per region (2^(coarse_shift - kSliceShift)).
-template <int MAXF>
+// slices per region (2^(coarse_shift - slice_shift)).  With LANES a slice
+// code is the 16-bit counting lane (counter << slice_shift) | cell of the
+// counting apply, else the 32-bit (cell << 6) | counter.
+template <int MAXF, bool LANES>
 __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p) {
     extern __shared__ uint32_t sorted[];   // the tile's codes grouped by slice
     __shared__ unsigned hist[MAXF], start[MAXF], fill[MAXF];
@@ -844,7 +846,11 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
         const unsigned long long b0 = base[f];
         if (b0 != ~0ull) {
             const uint64_t F = (uint64_t)b * fpc + f;
-            p.fine[F * p.fine_cap + b0 + (i - start[f])] = ((word & smask) << 6) | (code & 63u);
+            const uint64_t at = F * p.fine_cap + b0 + (i - start[f]);
+            if (LANES)
+                ((uint16_t *)p.fine)[at] = (uint16_t)(((code & 63u) << p.slice_shift) | (word & smask));
+            else
+                ((uint32_t *)p.fine)[at] = ((word & smask) << 6) | (code & 63u);
         } else {
             const uint64_t cell = ((uint64_t)b << p.coarse_shift) | word;
             sat_increment(p.G.cells, cell, (code & 63u) * (unsigned)p.G.alpha, p.G.maxc,
@@ -866,7 +872,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
     if (n == 0) return;   // no increments for this slice
     for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) cells_s[i] = p.G.cells[w0 + i];
     __syncthreads();
-    const uint32_t *src = p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
+    const uint32_t *src = (const uint32_t *)p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
     const uint32_t wmask = (uint32_t)(slice - 1);
     const uint64_t maxc = p.G.maxc;
     const unsigned alpha = (unsigned)p.G.alpha;
@@ -920,7 +926,10 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
 // The slice's increments are counted in 32-bit shared-memory lanes, counter
 // (cell, l) at lane l * 2^slice_shift + cell (a pass stages at most 2^31
 // increments, so a lane cannot wrap).  Then every counter becomes
-// min(old + count, 2^alpha - 1) and the slice is written back once.
+// min(old + count, 2^alpha - 1) and the slice is written back once.  With
+// LANES the codes are the 16-bit lanes themselves, else 32-bit
+// (cell << 6) | counter codes.
+template <bool LANES>
 __global__ void __launch_bounds__(kApplyThreads, 2) apply_count_kernel(ApplyArgs p) {
     extern __shared__ uint32_t lanes[];   // one 32-bit count per counter of the slice
     const uint64_t s = blockIdx.x;
@@ -934,35 +943,46 @@ __global__ void __launch_bounds__(kApplyThreads, 2) apply_count_kernel(ApplyArgs
     const unsigned nwords = eta << ssh;
     for (unsigned i = threadIdx.x; i < nwords; i += kApplyThreads) lanes[i] = 0;
     __syncthreads();
-    const uint32_t *src = p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
+    // 16 bytes per load: 8 lane codes or 4 cell codes; two loads per thread in flight
+    constexpr unsigned kPer = LANES ? 8 : 4;
+    constexpr unsigned kStep = kApplyThreads * 2 * kPer;
     const uint32_t wmask = (uint32_t)(slice - 1);
-    constexpr unsigned kStep = kApplyThreads * 8;
+    // each slice's codes start 16-byte aligned (cap: a multiple of 8 lanes, 4 cells)
+    const uint16_t *src16 = (const uint16_t *)p.codes + s * p.cap;
+    const uint32_t *src32 = (const uint32_t *)p.codes + s * p.cap;
     for (uint64_t i0 = 0; i0 < n; i0 += kStep) {
-        uint32_t code[8];
+        uint32_t code[2 * kPer];
         unsigned valid = 0;
-        const uint64_t i = i0 + threadIdx.x * 4ull;
+        const uint64_t i = i0 + threadIdx.x * (uint64_t)kPer;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const uint64_t j = i + (uint64_t)h * kApplyThreads * 4;
-            if (j + 4 <= n) {
-                const uint4 v = __ldcs((const uint4 *)(src + j));
-                code[4 * h] = v.x;
-                code[4 * h + 1] = v.y;
-                code[4 * h + 2] = v.z;
-                code[4 * h + 3] = v.w;
-                valid |= 0xFu << (4 * h);
-            } else {
+            const uint64_t j = i + (uint64_t)h * kApplyThreads * kPer;
+            if (j + kPer <= n) {
+                const uint4 v = __ldcs(LANES ? (const uint4 *)(src16 + j) : (const uint4 *)(src32 + j));
+                const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    code[4 * h + q] = j + q < n ? src[j + q] : 0u;
-                    valid |= (j + q < n ? 1u : 0u) << (4 * h + q);
+                    if (LANES) {
+                        code[kPer * h + 2 * q] = w[q] & 0xFFFFu;
+                        code[kPer * h + 2 * q + 1] = w[q] >> 16;
+                    } else {
+                        code[kPer * h + q] = w[q];
+                    }
+                }
+                valid |= ((1u << kPer) - 1) << (kPer * h);
+            } else {
+#pragma unroll
+                for (unsigned q = 0; q < kPer; ++q) {
+                    const bool in = j + q < n;
+                    code[kPer * h + q] = !in ? 0u : LANES ? (uint32_t)src16[j + q] : src32[j + q];
+                    valid |= (in ? 1u : 0u) << (kPer * h + q);
                 }
             }
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (unsigned q = 0; q < 2 * kPer; ++q) {
             if (!((valid >> q) & 1u)) continue;   // past the end
-            const unsigned c = ((code[q] & 63u) << ssh) | ((code[q] >> 6) & wmask);
+            const unsigned c = LANES ? code[q] : ((code[q] & 63u) << ssh) | ((code[q] >> 6) & wmask);
             atomicAdd(lanes + c, 1u);
         }
     }
@@ -1085,23 +1105,22 @@ cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s) {
         return cudaErrorInvalidValue;
     const int smem = kRepartTile * (int)sizeof(uint32_t);
     const dim3 grid((unsigned)tiles, kCoarseBins);
-    cudaError_t e;
-    if (p.coarse_shift - p.slice_shift <= 6) {
-        e = cudaFuncSetAttribute(repartition_kernel<64>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        repartition_kernel<64><<<grid, kRepartThreads, smem, s>>>(p);
-    } else {
-        e = cudaFuncSetAttribute(repartition_kernel<kMaxFine>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        repartition_kernel<kMaxFine><<<grid, kRepartThreads, smem, s>>>(p);
-    }
+    if (p.lane_codes && ((uint64_t)p.G.eta << p.slice_shift) > (uint64_t)kCountLanes)
+        return cudaErrorInvalidValue;   // a lane must fit 16 bits
+    const bool narrow = p.coarse_shift - p.slice_shift <= 6;
+    void (*k)(PartArgs) = narrow ? (p.lane_codes ? repartition_kernel<64, true>
+                                                 : repartition_kernel<64, false>)
+                                 : (p.lane_codes ? repartition_kernel<kMaxFine, true>
+                                                 : repartition_kernel<kMaxFine, false>);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kRepartThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
     if (nslices == 0) return cudaSuccess;
+    if (p.lane_codes || p.cap % 4) return cudaErrorInvalidValue;   // 32-bit codes, 16-byte aligned
     const size_t smem = (size_t)8 << p.slice_shift;
     cudaError_t e = cudaFuncSetAttribute(apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(8 << kSliceShift));
@@ -1114,11 +1133,12 @@ cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_
     if (nslices == 0) return cudaSuccess;
     const size_t smem = ((size_t)p.G.eta << p.slice_shift) * 4;
     if (smem > (size_t)kCountLanes * 4 || p.G.alpha > 15) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(apply_count_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (p.cap % (p.lane_codes ? 8 : 4)) return cudaErrorInvalidValue;   // 16-byte aligned slices
+    void (*k)(ApplyArgs) = p.lane_codes ? apply_count_kernel<true> : apply_count_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kCountLanes * 4);
     if (e != cudaSuccess) return e;
-    apply_count_kernel<<<(unsigned)nslices, kApplyThreads, smem, s>>>(p);
+    k<<<(unsigned)nslices, kApplyThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

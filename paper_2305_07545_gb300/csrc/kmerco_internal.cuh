@@ -270,8 +270,10 @@ struct PartArgs {
     const uint32_t *coarse;
     uint64_t coarse_cap;
     const unsigned long long *coarse_written;
-    uint32_t *fine;                        // one region of fine_cap codes per slice
+    void *fine;                            // one region of fine_cap codes per slice:
+                                           // uint16 lane codes when lane_codes, else uint32
     uint64_t fine_cap;
+    int lane_codes;                        // slice codes are counting-apply lanes
     unsigned long long *fine_cursor;
     unsigned long long *fine_written;
     DevCounters *ctr;
@@ -280,8 +282,10 @@ struct PartArgs {
 struct ApplyArgs {
     Geometry G;
     int slice_shift;                       // cells per slice = 2^slice_shift
-    const uint32_t *codes;                 // one region of cap codes per slice
+    const void *codes;                     // one region of cap codes per slice:
+                                           // uint16 lane codes when lane_codes, else uint32
     uint64_t cap;
+    int lane_codes;
     const unsigned long long *written;     // codes per slice
     DevCounters *ctr;
 };
