@@ -348,12 +348,55 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
             }
         }
 
-        // All loads of a group of four hashes (and, in the first group,
-        // the distinct-set home slot) are issued together, then all
-        // first compare-and-swap attempts; only failed attempts retry.
         uint64_t table_hash = 0, table_first = kEmptyKey - 1;
         const uint64_t k1m = KW == 1 ? premix8(klo) : 0;
-        for (int a0 = 0; a0 < G.nhash; a0 += 4) {
+        if (PART) {
+            // Partitioned design: stage one 32-bit code per increment, the
+            // cell within its coarse region (up to 24 bits) above the counter
+            // within the cell (6 bits), the region itself beside it.  A
+            // window's k_h codes sit together: one reservation per warp.  The
+            // hashes go two per loop trip (a smaller loop body measured
+            // faster than all k_h at once); the distinct-set home slot is
+            // loaded as soon as the first hash gives it.
+            const unsigned nh = (unsigned)G.nhash;   // at most kPartMaxHash
+            const unsigned bal = __ballot_sync(0xffffffffu, active);
+            unsigned base = 0;
+            if (lane == 0 && bal) base = atomicAdd(&S.nupd, nh * (unsigned)__popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            base += nh * (unsigned)__popc(bal & ((1u << lane) - 1));
+            if (active) {
+#pragma unroll 2
+                for (unsigned j = 0; j < nh; ++j) {
+                    uint64_t h1, h2, cell;
+                    unsigned slot;
+                    if (KW == 1)
+                        murmur8(k1m, j, h1, h2);
+                    else
+                        murmur16(klo, khi, j, h1, h2);
+                    if (j == 0) {
+                        table_hash = h2;
+                        if (KW == 1)
+                            table_first = load_hint(a.table + __umul64hi(table_hash, a.cap),
+                                                    pol_stream);
+                    }
+                    address(G, h1, cell, slot);
+                    const unsigned bin = (unsigned)(cell >> a.coarse_shift);
+                    const uint32_t code =
+                        ((uint32_t)(cell & ((1ull << a.coarse_shift) - 1)) << 6) | slot;
+                    if (PART == 2) {   // region beside the code
+                        S.staged[base + j] = code;
+                        S.sbin[base + j] = (uint8_t)bin;
+                    } else {           // region in the top 6 bits (coarse_shift <= 20)
+                        S.staged[base + j] = (bin << 26) | code;
+                    }
+                    atomicAdd(&S.hist[bin], 1u);
+                }
+            }
+        }
+        // Atomic design: all loads of a group of four hashes (and, in the
+        // first group, the distinct-set home slot) are issued together, then
+        // all first compare-and-swap attempts; only failed attempts retry.
+        for (int a0 = 0; !PART && a0 < G.nhash; a0 += 4) {
             uint64_t cell[4], cur[4], prev[4];
             unsigned sh[4], slot[4];
             bool use[4], need[4];
@@ -376,35 +419,6 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
             }
             if (KW == 1 && a0 == 0 && active)
                 table_first = load_hint(a.table + __umul64hi(table_hash, a.cap), pol_stream);
-            if (PART) {
-                // stage one 32-bit code per increment, cell within the coarse
-                // region (up to 24 bits) above the counter within the cell
-                // (6 bits); the region itself goes beside it.  The group's
-                // nh codes of a window sit together: one reservation per warp.
-                const unsigned nh = (unsigned)min(4, G.nhash - a0);
-                const unsigned bal = __ballot_sync(0xffffffffu, active);
-                unsigned base = 0;
-                if (lane == 0 && bal) base = atomicAdd(&S.nupd, nh * (unsigned)__popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                base += nh * (unsigned)__popc(bal & ((1u << lane) - 1));
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (use[j]) {
-                        const unsigned bin = (unsigned)(cell[j] >> a.coarse_shift);
-                        const unsigned at = base + (unsigned)j;
-                        const uint32_t code =
-                            ((uint32_t)(cell[j] & ((1ull << a.coarse_shift) - 1)) << 6) | slot[j];
-                        if (PART == 2) {   // region beside the code
-                            S.staged[at] = code;
-                            S.sbin[at] = (uint8_t)bin;
-                        } else {           // region in the top 6 bits (coarse_shift <= 20)
-                            S.staged[at] = (bin << 26) | code;
-                        }
-                        atomicAdd(&S.hist[bin], 1u);
-                    }
-                }
-                continue;
-            }
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (use[j]) cur[j] = load_hint(G.cells + cell[j], pol_keep);
