@@ -134,18 +134,26 @@ __global__ void __launch_bounds__(kSortThreads) scan_rows_kernel(uint32_t *count
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
+// The scatter of one pass: the same tiles as upsweep_kernel, taken by
+// kDownThreads threads (fewer keys per thread than the upsweep, so that two
+// blocks fit an SM's registers).
+constexpr int kDownThreads = 512;
+
 template <int KW>
-__global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint64_t *in, uint64_t *out,
-                                                                 uint64_t n, int shift,
-                                                                 const uint32_t *counts,
-                                                                 const uint32_t *totals,
-                                                                 uint32_t ntiles) {
-    constexpr int ITEMS = kSortItems / KW;
+__global__ void __launch_bounds__(kDownThreads, 2) downsweep_kernel(const uint64_t *in, uint64_t *out,
+                                                                    uint64_t n, int shift,
+                                                                    const uint32_t *counts,
+                                                                    const uint32_t *totals,
+                                                                    uint32_t ntiles) {
     constexpr int TILE = tile_keys<KW>();
-    __shared__ uint32_t wcnt[kWarps][kRadixBins];
+    constexpr int ITEMS = TILE / kDownThreads;
+    constexpr int NW = kDownThreads / 32;
+    static_assert(kRadixBins <= kDownThreads, "one thread per digit");
+    __shared__ uint16_t wcnt[NW][kRadixBins];   // a tile's counts and offsets stay below 2^16
     __shared__ uint32_t tstart[kRadixBins];
     __shared__ uint64_t gofs[kRadixBins];
     __shared__ uint64_t stage[TILE * KW];
+    static_assert(TILE < 65536, "16-bit warp counts");
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t tile_base = (uint64_t)blockIdx.x * TILE;
@@ -181,7 +189,7 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint64_t 
         }
         const unsigned prev = wcnt[warp][dig[j]];
         __syncwarp();
-        if (lane == __ffs(peers) - 1) wcnt[warp][dig[j]] = prev + __popc(peers);
+        if (lane == __ffs(peers) - 1) wcnt[warp][dig[j]] = (uint16_t)(prev + __popc(peers));
         __syncwarp();
         rank[j] = prev + __popc(peers & lt);
     }
@@ -191,17 +199,24 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint64_t 
     {
         const int d = tid;
         uint32_t run = 0;
+        uint64_t t64 = 0;
+        if (d < kRadixBins) {
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            uint32_t c = wcnt[w][d];
-            wcnt[w][d] = run;
-            run += c;
+            for (int w = 0; w < NW; ++w) {
+                uint32_t c = wcnt[w][d];
+                wcnt[w][d] = (uint16_t)run;
+                run += c;
+            }
+            t64 = totals[d];
         }
         uint32_t tot;
-        tstart[d] = block_exclusive_scan<uint32_t>(run, tot);
-        uint64_t t64 = totals[d], dtot;
-        uint64_t dbase = block_exclusive_scan<uint64_t>(t64, dtot);
-        gofs[d] = dbase + counts[(uint64_t)d * ntiles + blockIdx.x];
+        const uint32_t ts = block_exclusive_scan_n<uint32_t, kDownThreads>(run, tot);
+        uint64_t dtot;
+        const uint64_t dbase = block_exclusive_scan_n<uint64_t, kDownThreads>(t64, dtot);
+        if (d < kRadixBins) {
+            tstart[d] = ts;
+            gofs[d] = dbase + counts[(uint64_t)d * ntiles + blockIdx.x];
+        }
     }
     __syncthreads();
 
@@ -218,7 +233,7 @@ __global__ void __launch_bounds__(kSortThreads) downsweep_kernel(const uint64_t 
 
     const uint64_t left = n - tile_base;
     const unsigned valid = left < (uint64_t)TILE ? (unsigned)left : (unsigned)TILE;
-    for (unsigned i = tid; i < valid; i += kSortThreads) {
+    for (unsigned i = tid; i < valid; i += kDownThreads) {
         const unsigned d = digit_of<KW>(stage + i * KW, shift);
         const uint64_t o = gofs[d] + (i - tstart[d]);
 #pragma unroll
@@ -692,12 +707,12 @@ cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint6
         if (kw == 1) {
             upsweep_kernel<1><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
             scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
-            downsweep_kernel<1><<<ntiles, kSortThreads, 0, s>>>(src, dst, n, shift, counts, totals,
+            downsweep_kernel<1><<<ntiles, kDownThreads, 0, s>>>(src, dst, n, shift, counts, totals,
                                                                 ntiles);
         } else {
             upsweep_kernel<2><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
             scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
-            downsweep_kernel<2><<<ntiles, kSortThreads, 0, s>>>(src, dst, n, shift, counts, totals,
+            downsweep_kernel<2><<<ntiles, kDownThreads, 0, s>>>(src, dst, n, shift, counts, totals,
                                                                 ntiles);
         }
         cudaError_t e = cudaGetLastError();
