@@ -134,21 +134,22 @@ __global__ void __launch_bounds__(kSortThreads) scan_rows_kernel(uint32_t *count
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-// The scatter of one pass: the same tiles as upsweep_kernel, taken by
-// kDownThreads threads (fewer keys per thread than the upsweep, so that two
-// blocks fit an SM's registers).
-constexpr int kDownThreads = 512;
+// The scatter of one pass: the same tiles as upsweep_kernel.  One-word keys
+// take 512 threads, 8 keys each (two blocks of 16 warps fit an SM's
+// registers; 256 threads x 16 keys needed 118 registers); two-word keys
+// take 256 threads, 8 keys each, which measured faster than 512 x 4.
+template <int KW>
+__host__ __device__ constexpr int down_threads() { return KW == 1 ? 512 : 256; }
 
 template <int KW>
-__global__ void __launch_bounds__(kDownThreads, 2) downsweep_kernel(const uint64_t *in, uint64_t *out,
-                                                                    uint64_t n, int shift,
-                                                                    const uint32_t *counts,
-                                                                    const uint32_t *totals,
-                                                                    uint32_t ntiles) {
+__global__ void __launch_bounds__(down_threads<KW>(), KW == 1 ? 2 : 3) downsweep_kernel(
+    const uint64_t *in, uint64_t *out, uint64_t n, int shift, const uint32_t *counts,
+    const uint32_t *totals, uint32_t ntiles) {
+    constexpr int NT = down_threads<KW>();
     constexpr int TILE = tile_keys<KW>();
-    constexpr int ITEMS = TILE / kDownThreads;
-    constexpr int NW = kDownThreads / 32;
-    static_assert(kRadixBins <= kDownThreads, "one thread per digit");
+    constexpr int ITEMS = TILE / NT;
+    constexpr int NW = NT / 32;
+    static_assert(kRadixBins <= NT, "one thread per digit");
     __shared__ uint16_t wcnt[NW][kRadixBins];   // a tile's counts and offsets stay below 2^16
     __shared__ uint32_t tstart[kRadixBins];
     __shared__ uint64_t gofs[kRadixBins];
@@ -210,9 +211,9 @@ __global__ void __launch_bounds__(kDownThreads, 2) downsweep_kernel(const uint64
             t64 = totals[d];
         }
         uint32_t tot;
-        const uint32_t ts = block_exclusive_scan_n<uint32_t, kDownThreads>(run, tot);
+        const uint32_t ts = block_exclusive_scan_n<uint32_t, NT>(run, tot);
         uint64_t dtot;
-        const uint64_t dbase = block_exclusive_scan_n<uint64_t, kDownThreads>(t64, dtot);
+        const uint64_t dbase = block_exclusive_scan_n<uint64_t, NT>(t64, dtot);
         if (d < kRadixBins) {
             tstart[d] = ts;
             gofs[d] = dbase + counts[(uint64_t)d * ntiles + blockIdx.x];
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kDownThreads, 2) downsweep_kernel(const uint64
 
     const uint64_t left = n - tile_base;
     const unsigned valid = left < (uint64_t)TILE ? (unsigned)left : (unsigned)TILE;
-    for (unsigned i = tid; i < valid; i += kDownThreads) {
+    for (unsigned i = tid; i < valid; i += NT) {
         const unsigned d = digit_of<KW>(stage + i * KW, shift);
         const uint64_t o = gofs[d] + (i - tstart[d]);
 #pragma unroll
@@ -707,12 +708,12 @@ cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint6
         if (kw == 1) {
             upsweep_kernel<1><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
             scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
-            downsweep_kernel<1><<<ntiles, kDownThreads, 0, s>>>(src, dst, n, shift, counts, totals,
+            downsweep_kernel<1><<<ntiles, down_threads<1>(), 0, s>>>(src, dst, n, shift, counts, totals,
                                                                 ntiles);
         } else {
             upsweep_kernel<2><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
             scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
-            downsweep_kernel<2><<<ntiles, kDownThreads, 0, s>>>(src, dst, n, shift, counts, totals,
+            downsweep_kernel<2><<<ntiles, down_threads<2>(), 0, s>>>(src, dst, n, shift, counts, totals,
                                                                 ntiles);
         }
         cudaError_t e = cudaGetLastError();
