@@ -28,7 +28,8 @@
 //    cursor atomic per region and chunk.  repartition_kernel splits every
 //    region into slices, and one block per slice applies its increments in
 //    shared memory: apply_count_kernel (alpha <= 15) counts them in 32-bit
-//    lanes and adds the counts with saturation, apply_kernel uses
+//    lanes and adds the counts with saturation (the repartition then writes
+//    each increment as its 16-bit lane index), apply_kernel uses
 //    shared-memory compare-and-swap on the cells.  Either writes the slice
 //    back once.  Increments that do not fit a buffer fall back to the global
 //    compare-and-swap.
