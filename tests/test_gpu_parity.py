@@ -143,6 +143,9 @@ UPDATE_CASES = [
     (21, 3 * (1 << 23) + 48, 4, 4, 2), # non power-of-two m, partial last slice
     (17, 12 << 20, 5, 4, 3),           # eta = 12
     (25, 1 << 24, 8, 2, 3),            # eta = 8, k_h = 2
+    (21, 1 << 27, 1, 3, 0),            # eta = 64: 2^21 cells, 16-bit lanes (counter << 7) | cell
+    (15, 1 << 26, 2, 2, 1),            # eta = 32: lanes (counter << 8) | cell
+    (19, 21 << 20, 3, 4, 2),           # eta = 21, not a power of two: lanes (counter << 9) | cell
 ]
 
 
