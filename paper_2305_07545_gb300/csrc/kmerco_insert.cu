@@ -513,7 +513,7 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
             for (unsigned i = lane; i < n; i += 32) {
                 const uint32_t code = S.sorted[s0 + i];
                 if (dst) {
-                    dst[i] = code;
+                    __stcs(dst + i, code);
                 } else {
                     const uint64_t cell = ((uint64_t)bin << a.coarse_shift) | (code >> 6);
                     const unsigned shift = (code & 63u) * (unsigned)G.alpha;
@@ -863,9 +863,10 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
             const uint64_t F = (uint64_t)b * fpc + f;
             const uint64_t at = F * p.fine_cap + b0 + (i - start[f]);
             if (LANES)
-                ((uint16_t *)p.fine)[at] = (uint16_t)(((code & 63u) << p.slice_shift) | (word & smask));
+                __stcs((unsigned short *)p.fine + at,
+                       (unsigned short)(((code & 63u) << p.slice_shift) | (word & smask)));
             else
-                ((uint32_t *)p.fine)[at] = ((word & smask) << 6) | (code & 63u);
+                __stcs((uint32_t *)p.fine + at, ((word & smask) << 6) | (code & 63u));
         } else {
             const uint64_t cell = ((uint64_t)b << p.coarse_shift) | word;
             sat_increment(p.G.cells, cell, (code & 63u) * (unsigned)p.G.alpha, p.G.maxc,
