@@ -94,6 +94,34 @@ def recorded_traffic() -> float | None:
     return None
 
 
+def roofline_of_insert(inserted: int, distinct: int, nhash: int, input_bytes: int,
+                       insert_ms: float, peak_gbs: float, traffic: float | None) -> dict:
+    """Roofline of one insert call.  Its algorithmic bytes follow the HBM
+    random-sector bound of the countBF update: each of a K-mer's k_h counter
+    updates reads one random 32-byte sector and writes it back (64 B).  The
+    word-granular count beside it takes an 8-byte cell read and written per
+    update, one 8-byte distinct-set probe per K-mer, the input and 16 B per
+    new key."""
+    insert_s = insert_ms / 1000.0
+    kmer_bytes = 64 * nhash
+    launch_bytes = inserted * kmer_bytes
+    achieved = launch_bytes / insert_s / 1e9
+    word_bytes = input_bytes + inserted * (16 * nhash + 8) + distinct * 16
+    return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+            "frac": achieved / peak_gbs, "traffic": traffic,
+            "kernel": "insert phase: every kernel of one kmerco_insert call (insert_kernel: "
+                      "pack, canonical, hash, distinct set, increment staging; in the "
+                      "partitioned design also repartition_kernel and the apply kernel)",
+            "model": "HBM random-sector bound of the countBF update: 64 B per counter "
+                     "update (a 32-byte sector read and written back), k_h per K-mer",
+            "algorithmic_bytes_per_kmer": kmer_bytes,
+            "algorithmic_bytes_per_launch": int(launch_bytes),
+            "word_granular": {"bytes_per_launch": int(word_bytes),
+                              "achieved": word_bytes / insert_s / 1e9,
+                              "frac": word_bytes / insert_s / 1e9 / peak_gbs},
+            "avg_launch_ms": insert_ms}
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -353,31 +381,12 @@ def run_ours(args) -> None:
 
     peak, peak_src = measured_peak()
     avg_insert_ms = statistics.mean(insert_ms)
-    insert_s = avg_insert_ms / 1000.0
-    # HBM random-sector bound of the countBF update: each of a K-mer's k_h
-    # counter updates reads one random 32-byte sector and writes it back
-    kmer_bytes = 64 * w.nhash
-    launch_bytes = inserted * kmer_bytes
-    achieved = launch_bytes / insert_s / 1e9
-    # word-granular count: an 8-byte cell read and written per update, one
-    # 8-byte distinct-set probe per K-mer, the input and the new keys
-    word_bytes = bases.nbytes + offsets.nbytes + inserted * (16 * w.nhash + 8) + distinct * 16
     # the ncu record covers the full `single` call only
     traffic = recorded_traffic() if args.workload == "single" and not args.reads else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "insert phase: every kernel of one kmerco_insert call (insert_kernel: "
-                          "pack, canonical, hash, distinct set, increment staging; in the "
-                          "partitioned design also repartition_kernel and the apply kernel)",
-                "model": "HBM random-sector bound of the countBF update: 64 B per counter "
-                         "update (a 32-byte sector read and written back), k_h per K-mer",
-                "algorithmic_bytes_per_kmer": kmer_bytes,
-                "algorithmic_bytes_per_launch": int(launch_bytes),
-                "word_granular": {"bytes_per_launch": int(word_bytes),
-                                  "achieved": word_bytes / insert_s / 1e9,
-                                  "frac": word_bytes / insert_s / 1e9 / peak},
-                "avg_launch_ms": avg_insert_ms, "insert_share_of_step": avg_insert_ms / (total_ms / args.steps),
-                "peak_source": peak_src}
+    roofline = roofline_of_insert(inserted, distinct, w.nhash, bases.nbytes + offsets.nbytes,
+                                  avg_insert_ms, peak, traffic)
+    roofline["insert_share_of_step"] = avg_insert_ms / (total_ms / args.steps)
+    roofline["peak_source"] = peak_src
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
