@@ -95,7 +95,9 @@ typedef struct {
     uint64_t pass_codes;   /* partitioned design: counter increments staged per pass, 1..2^31;
                               0: 2^31.  A batch with more increments is inserted in several
                               passes over consecutive parts of its reads; smaller values bound
-                              the scratch memory (about 10 bytes per staged increment). */
+                              the scratch memory (about 7 bytes per staged increment with the
+                              counting apply: a 4-byte region code and a 2-byte slice code,
+                              with headroom; about 10 with the compare-and-swap apply). */
 } kmerco_config_t;
 
 /* Running totals and results of one handle (kmerco_stats). */
