@@ -5,7 +5,12 @@ insert every read (pack, canonicalise, hash, saturating counter updates,
 distinct-key set), then classify (sort the distinct keys, QcountBF-II per
 key, split at tau).  value = K-mer windows inserted / step time.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload single]
+The default workload is the largest single-GPU one: 20,000,000 reads x 150 bp
+of a 100 Mb genome with repeat families, a 2^33-counter (4 GiB) countBF,
+counted as 31-mers; the same reads counted as 55-mers (two-word keys) are
+timed after it and reported under "secondary".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload repeats]
     python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 Under torchrun (N > 1) every rank counts its own sample (a different seed)
@@ -37,6 +42,10 @@ UNIT = "K-mer insertions/s"
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 256 << 20
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "insert_phase_single.md")
+# per workload: the ncu summary holding the DRAM traffic record of its insert phase
+PROFILE_SUMMARIES = {"single": PROFILE_SUMMARY,
+                     "repeats": os.path.join(ROOT, "profiles", "insert_phase_repeats.md")}
+SECONDARY = {"repeats": "repeats55"}   # workload timed after the headline one, same reads
 INSERT_SOURCES = [os.path.join(ROOT, "paper_2305_07545_gb300", "csrc", f)
                   for f in ("kmerco_insert.cu", "kmerco_internal.cuh")]
 
@@ -79,11 +88,14 @@ def measured_peak() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback (6.8 TB/s earlier GB300 copy measurement)"
 
 
-def recorded_traffic() -> float | None:
-    """DRAM bytes per insert launch from the committed ncu summary, if it was
-    taken on the current insert-kernel source."""
+def recorded_traffic(workload: str = "single") -> float | None:
+    """DRAM bytes per insert call from the committed ncu summary of the
+    workload, if it was taken on the current insert-kernel source."""
+    path = PROFILE_SUMMARIES.get(workload)
+    if not path:
+        return None
     try:
-        with open(PROFILE_SUMMARY) as f:
+        with open(path) as f:
             for line in f:
                 if line.startswith("traffic_record"):
                     kv = dict(p.split("=", 1) for p in line.split()[1:])
@@ -94,32 +106,81 @@ def recorded_traffic() -> float | None:
     return None
 
 
-def roofline_of_insert(inserted: int, distinct: int, nhash: int, input_bytes: int,
+def roofline_of_insert(inserted: int, nhash: int, key_words: int, input_bytes: int,
                        insert_ms: float, peak_gbs: float, traffic: float | None) -> dict:
-    """Roofline of one insert call.  Its algorithmic bytes follow the HBM
-    random-sector bound of the countBF update: each of a K-mer's k_h counter
-    updates reads one random 32-byte sector and writes it back (64 B).  The
-    word-granular count beside it takes an 8-byte cell read and written per
-    update, one 8-byte distinct-set probe per K-mer, the input and 16 B per
-    new key."""
+    """Roofline of one insert call (every kernel of one kmerco_insert).
+
+    Algorithmic bytes, word-granular: per inserted K-mer k_h read-modify-writes
+    of one 8-byte countBF cell (16 B each) and its canonical key written once
+    and read once by the exact distinct step (8 B per key word each way), plus
+    the input bases and offsets.  The HBM random-sector model (each update
+    reads a random 32-byte sector and writes it back: 64 B per update) is
+    reported beside it as a secondary bound, not the headline."""
     insert_s = insert_ms / 1000.0
-    kmer_bytes = 64 * nhash
-    launch_bytes = inserted * kmer_bytes
+    per_kmer = 16 * nhash + 16 * key_words
+    launch_bytes = input_bytes + inserted * per_kmer
     achieved = launch_bytes / insert_s / 1e9
-    word_bytes = input_bytes + inserted * (16 * nhash + 8) + distinct * 16
+    sector_bytes = inserted * 64 * nhash
     return {"bound": "hbm", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
             "frac": achieved / peak_gbs, "traffic": traffic,
             "kernel": "insert phase: every kernel of one kmerco_insert call (insert_kernel: "
                       "pack, canonical, hash, distinct set, increment staging; in the "
                       "partitioned design also repartition_kernel and the apply kernel)",
-            "model": "HBM random-sector bound of the countBF update: 64 B per counter "
-                     "update (a 32-byte sector read and written back), k_h per K-mer",
-            "algorithmic_bytes_per_kmer": kmer_bytes,
+            "model": "word-granular: k_h x (8-byte cell read + write) + key written and "
+                     "read once per inserted K-mer, plus the input",
+            "algorithmic_bytes_per_kmer": per_kmer,
             "algorithmic_bytes_per_launch": int(launch_bytes),
-            "word_granular": {"bytes_per_launch": int(word_bytes),
-                              "achieved": word_bytes / insert_s / 1e9,
-                              "frac": word_bytes / insert_s / 1e9 / peak_gbs},
+            "traffic_over_algorithmic": (traffic / launch_bytes) if traffic else None,
+            "sector_model": {"bytes_per_kmer": 64 * nhash,
+                             "bytes_per_launch": int(sector_bytes),
+                             "achieved": sector_bytes / insert_s / 1e9,
+                             "frac": sector_bytes / insert_s / 1e9 / peak_gbs,
+                             "note": "HBM random-sector bound of an in-place update design "
+                                     "(64 B per counter update); secondary"},
             "avg_launch_ms": insert_ms}
+
+
+def l2_atomic_roofline(inserted: int, nhash: int, insert_ms: float, cas_peak: float) -> dict:
+    """The countBF update against the measured random compare-and-swap rate
+    on an L2-resident buffer: k_h updates per inserted K-mer."""
+    ups = inserted * nhash / (insert_ms / 1000.0)
+    return {"bound": "l2_atomic", "achieved": ups / 1e9, "peak": cas_peak / 1e9,
+            "unit": "G updates/s", "frac": ups / cas_peak, "traffic": None,
+            "model": "k_h counter updates per inserted K-mer over the insert phase",
+            "avg_launch_ms": insert_ms}
+
+
+def measure_peaks(device: int) -> dict:
+    """Random 64-bit load+CAS and random 8-byte read rates on this GPU
+    (kmerco_peak_*), over an L2-resident buffer, a 128 MiB one and a 4 GiB
+    one: the ceilings of the countBF update and query."""
+    import paper_2305_07545_gb300 as kc
+    out = {}
+    for name, nbytes in (("512KiB", 512 << 10), ("128MiB", 128 << 20), ("4GiB", 4 << 30)):
+        out[name] = {"random_cas_per_s": kc.kmerco_peak_random_cas(nbytes, 1 << 28, device),
+                     "random_read_per_s": kc.kmerco_peak_random_read(nbytes, 1 << 28, device)}
+    return out
+
+
+def host_cpu() -> dict:
+    """CPU model and logical core count of the host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":", 1)[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            import platform
+            model = platform.processor() or platform.machine()
+        except Exception:
+            model = "unknown"
+    return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
 class ClockSampler:
@@ -193,18 +254,24 @@ def cpu_oracle_rate(bases, offsets, w, n_reads: int) -> dict:
     dhi, dlo, _ = oracle.distinct(ex.hi, ex.lo)
     oracle.classify(filt, dhi, dlo, w.K, w.m, w.alpha, w.nhash, w.tau)
     dt = time.perf_counter() - t0
+    del filt
     # untimed: Algorithm 1's sequential first-seen count (query 0 before the
     # insert) against the exact distinct count, on the first 2e6 K-mers
     n2 = min(ex.n, 2_000_000)
     first_seen = oracle.seq_distinct(ex.hi[:n2], ex.lo[:n2], w.K, w.m, w.alpha, w.nhash)
     exact = len(oracle.distinct(ex.hi[:n2], ex.lo[:n2])[1])
     return {"value": ex.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "seconds": round(dt, 3),
+            "seconds": round(dt, 3), **host_cpu(),
             "sample": f"first {n_reads:,} reads of the workload ({ex.n:,} K-mers): oracle "
                       f"extraction + sequential Algorithm 3 + sort/unique + Algorithm 2, "
                       f"single-threaded C on the host",
             "distinct_first_K_mers": {"kmers": n2, "exact": exact,
                                       "sequential_first_seen": first_seen}}
+
+
+# reads per bounded oracle sample, per workload: about 10-20 s of one host core
+CPU_READS = {"tiny": 2_000, "single": 150_000, "repeats": 40_000, "repeats55": 40_000}
+REF_READS = {"tiny": 2_000, "single": 25_000, "repeats": 10_000, "repeats55": 10_000}
 
 
 def dist_setup():
@@ -236,7 +303,7 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     w = readsim.WORKLOADS[args.workload]
-    sample = args.ref_reads
+    sample = args.ref_reads or REF_READS.get(args.workload, 25_000)
     wl = readsim.scaled(args.workload, sample)
     bases, offsets = wl.generate()
     import oracle
@@ -255,38 +322,27 @@ def run_reference(args) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": describe(w), "sample_reads_per_step": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": rates[0]["sample"] + ", per step"},
+                             **host_cpu(), "sample": rates[0]["sample"] + ", per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args) -> None:
+def time_workload(name: str, args, bases, offsets, d_bases, d_offsets, flush, clock_dev,
+                  world: int, e2e: bool) -> dict:
+    """Warm-up and timed steps of one workload on the already resident reads;
+    optionally the end-to-end steps from pinned host buffers."""
     import torch
     import torch.distributed as dist
 
     import paper_2305_07545_gb300 as kc
 
-    world, rank, local = dist_setup()
-    if world > 1:
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    w = readsim.WORKLOADS[name]
     dev = torch.cuda.current_device()
-    w = readsim.WORKLOADS[args.workload]
-    wl = readsim.scaled(args.workload, args.reads or w.reads.n_reads, seed_offset=rank)
-    bases, offsets = wl.generate()
     nreads = len(offsets) - 1
     lens = np.diff(offsets.astype(np.int64))
     windows_expected = int(np.maximum(lens - w.K + 1, 0).sum())
-
     stream = torch.cuda.current_stream()
-    d_bases = torch.from_numpy(bases).to(dev)
-    d_offsets = torch.from_numpy(offsets.view(np.int64)).to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    torch.cuda.synchronize()
-
     bf = kc.CountBF(w.K, w.m, w.alpha, w.nhash, w.tau, stream=stream.cuda_stream)
 
     def step():
@@ -307,7 +363,7 @@ def run_ours(args) -> None:
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    with ClockSampler(dev if world == 1 else local) as clk:
+    with ClockSampler(clock_dev) as clk:
         for i in range(args.steps):
             flush.zero_()
             l0 = bf.stats()["launches"]
@@ -324,11 +380,14 @@ def run_ours(args) -> None:
     total_ms = max_over_ranks(sum(step_ms), dev)
     if world > 1:
         dist.barrier()
-    value = whole_job_rate(inserted, args.steps, world, total_ms / 1000.0)
+    out = {"workload": w, "inserted": inserted, "distinct": distinct, "trusted": trusted,
+           "total_ms": total_ms, "insert_ms": statistics.mean(insert_ms),
+           "classify_ms": statistics.mean(classify_ms), "launches": launches,
+           "clocks": clk.summary(), "e2e": None,
+           "device_bytes": bf.stats()["device_bytes"]}
 
     # end to end through the public API with host (pinned) buffers
-    e2e = None
-    if not args.no_e2e:
+    if e2e:
         h_bases = torch.from_numpy(bases).pin_memory()
         h_offsets = torch.from_numpy(offsets.view(np.int64)).pin_memory()
         cap = max(distinct, 1)
@@ -366,49 +425,126 @@ def run_ours(args) -> None:
         torch.cuda.synchronize()
         e2e_s = max_over_ranks(time.perf_counter() - t0, dev)
         assert nt == trusted and nt + ne == distinct
-        e2e = {"value": whole_job_rate(inserted, args.steps, world, e2e_s), "unit": UNIT,
-               "h2d_bytes_per_step": int(bases.nbytes + offsets.nbytes),
-               "d2h_bytes_per_step": int(8 * kw * distinct),
-               "note": "reset + insert from pinned host reads + classify + copy of the "
-                       "trustworthy and erroneous key lists to pinned host memory; wall clock",
-               "host_ms_per_step": {k: 1000.0 * v / args.steps for k, v in split.items()}}
-
+        out["e2e"] = {"value": whole_job_rate(inserted, args.steps, world, e2e_s), "unit": UNIT,
+                      "h2d_bytes_per_step": int(bases.nbytes + offsets.nbytes),
+                      "d2h_bytes_per_step": int(8 * kw * distinct),
+                      "note": "reset + insert from pinned host reads + classify + copy of the "
+                              "trustworthy and erroneous key lists to pinned host memory; "
+                              "wall clock",
+                      "host_ms_per_step": {k: 1000.0 * v / args.steps for k, v in split.items()}}
+        del h_bases, h_offsets, h_tr, h_er
     bf.close()
+    return out
+
+
+def workload_roofline(r: dict, name: str, input_bytes: int, peak: float, peak_src: str,
+                      peaks: dict | None, full_size: bool) -> dict:
+    w = r["workload"]
+    kw = 1 if w.K <= 32 else 2
+    traffic = recorded_traffic(name) if full_size else None
+    roof = roofline_of_insert(r["inserted"], w.nhash, kw, input_bytes, r["insert_ms"], peak,
+                              traffic)
+    roof["insert_share_of_step"] = r["insert_ms"] / (r["total_ms"] / r["steps"])
+    roof["peak_source"] = peak_src + "; frac of measured"
+    if peaks:
+        cas = peaks["512KiB"]["random_cas_per_s"]
+        roof["l2_atomic"] = l2_atomic_roofline(r["inserted"], w.nhash, r["insert_ms"], cas)
+        if w.m * w.alpha // 8 <= (1 << 20):   # L2-resident countBF: the update is L2-atomic bound
+            l2 = roof.pop("l2_atomic")
+            l2["hbm_view"] = roof
+            roof = l2
+    return roof
+
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_setup()
+    name = args.workload
+    w = readsim.WORKLOADS[name]
+    # reads are generated (threads on the host) before CUDA starts
+    wl = readsim.scaled(name, args.reads or w.reads.n_reads, seed_offset=rank)
+    t_gen = time.perf_counter()
+    bases, offsets = wl.generate()
+    t_gen = time.perf_counter() - t_gen
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    clock_dev = dev if world == 1 else local
+
+    peaks = None if args.no_peaks else measure_peaks(dev)
+    d_bases = torch.from_numpy(bases).to(dev)
+    d_offsets = torch.from_numpy(offsets.view(np.int64)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+
+    full_size = not args.reads
+    input_bytes = bases.nbytes + offsets.nbytes
+    peak, peak_src = measured_peak()
+    r = time_workload(name, args, bases, offsets, d_bases, d_offsets, flush, clock_dev, world,
+                      e2e=not args.no_e2e)
+    r["steps"] = args.steps
+    value = whole_job_rate(r["inserted"], args.steps, world, r["total_ms"] / 1000.0)
+
+    secondary = None
+    sec_name = SECONDARY.get(name) if not args.no_secondary else None
+    if sec_name:
+        r2 = time_workload(sec_name, args, bases, offsets, d_bases, d_offsets, flush, clock_dev,
+                           world, e2e=False)
+        r2["steps"] = args.steps
+        w2 = r2["workload"]
+        secondary = {
+            "workload": describe(readsim.scaled(sec_name, len(offsets) - 1, seed_offset=rank)),
+            "K": w2.K, "value": whole_job_rate(r2["inserted"], args.steps, world,
+                                                r2["total_ms"] / 1000.0),
+            "unit": UNIT, "ms_per_step": r2["total_ms"] / args.steps,
+            "kmers_per_step_per_gpu": r2["inserted"], "distinct_per_gpu": r2["distinct"],
+            "trustworthy_per_gpu": r2["trusted"],
+            "phases": {"insert_ms": r2["insert_ms"], "classify_ms": r2["classify_ms"]},
+            "roofline": workload_roofline(r2, sec_name, input_bytes, peak, peak_src, peaks,
+                                          full_size),
+            "gpu_launches": r2["launches"], "clocks": r2["clocks"],
+            "device_bytes": r2["device_bytes"]}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    peak, peak_src = measured_peak()
-    avg_insert_ms = statistics.mean(insert_ms)
-    # the ncu record covers the full `single` call only
-    traffic = recorded_traffic() if args.workload == "single" and not args.reads else None
-    roofline = roofline_of_insert(inserted, distinct, w.nhash, bases.nbytes + offsets.nbytes,
-                                  avg_insert_ms, peak, traffic)
-    roofline["insert_share_of_step"] = avg_insert_ms / (total_ms / args.steps)
-    roofline["peak_source"] = peak_src
-
+    roofline = workload_roofline(r, name, input_bytes, peak, peak_src, peaks, full_size)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(bases, offsets, w, args.cpu_reads)
+        cpu = cpu_oracle_rate(bases, offsets, w, args.cpu_reads or CPU_READS.get(name, 50_000))
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": describe(wl), "K": w.K, "m": w.m, "counter_bits": w.alpha,
-                       "nhash": w.nhash, "tau": w.tau, "reads_per_gpu": nreads,
-                       "kmers_per_step_per_gpu": inserted, "distinct_per_gpu": distinct,
-                       "trustworthy_per_gpu": trusted,
+                       "nhash": w.nhash, "tau": w.tau, "reads_per_gpu": len(offsets) - 1,
+                       "kmers_per_step_per_gpu": r["inserted"], "distinct_per_gpu": r["distinct"],
+                       "trustworthy_per_gpu": r["trusted"],
                        "parallelism": f"{world} independent samples, one per GPU",
                        "l2": "256 MiB buffer written between timed steps, outside the "
-                             "per-step CUDA events; countBF 128 MiB + distinct set > L2"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "phases": {"insert_ms": statistics.mean(insert_ms),
-                       "classify_ms": statistics.mean(classify_ms),
-                       "insert_kmers_per_s": inserted / (statistics.mean(insert_ms) / 1000.0),
-                       "classify_distinct_per_s": distinct / (statistics.mean(classify_ms) / 1000.0)},
-            "gpu_launches": launches, "clocks": clk.summary()}
+                             "per-step CUDA events; inputs and countBF larger than L2",
+                       "device_bytes": r["device_bytes"],
+                       "read_generation_s": round(t_gen, 1)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": r["e2e"],
+            "phases": {"insert_ms": r["insert_ms"], "classify_ms": r["classify_ms"],
+                       "insert_kmers_per_s": r["inserted"] / (r["insert_ms"] / 1000.0),
+                       "classify_distinct_per_s": r["distinct"] / (r["classify_ms"] / 1000.0)},
+            "secondary": secondary,
+            "l2_atomic_peak": None if not peaks else {
+                "random_cas_per_s": {k: v["random_cas_per_s"] for k, v in peaks.items()},
+                "source": "kmerco_peak_random_cas: random 64-bit load + atomicCAS, measured "
+                          "in this run"},
+            "random_read_peak": None if not peaks else {
+                "random_read_per_s": {k: v["random_read_per_s"] for k, v in peaks.items()},
+                "source": "kmerco_peak_random_read: random 8-byte loads, measured in this run"},
+            "gpu_launches": r["launches"], "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -577,10 +713,10 @@ def run_serving(args) -> None:
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="single",
+    ap.add_argument("--workload", default="repeats",
                     choices=sorted(readsim.WORKLOADS) + ["batched", "serving"])
     ap.add_argument("--jobs", type=int, default=64, help="serving workload: jobs")
     ap.add_argument("--slots", type=int, default=16, help="serving workload: concurrent jobs")
@@ -589,14 +725,18 @@ def main(argv=None) -> None:
     ap.add_argument("--samples", type=int, default=256, help="batched workload: samples")
     ap.add_argument("--batch-scale", type=float, default=0.25,
                     help="batched workload: factor on every sample's read count")
-    ap.add_argument("--cpu-reads", type=int, default=150_000,
-                    help="reads in the bounded CPU-oracle sample")
-    ap.add_argument("--ref-reads", type=int, default=25_000,
-                    help="reads per step of the reference (oracle) arm")
+    ap.add_argument("--cpu-reads", type=int, default=0,
+                    help="reads in the bounded CPU-oracle sample (default: per workload)")
+    ap.add_argument("--ref-reads", type=int, default=0,
+                    help="reads per step of the reference (oracle) arm (default: per workload)")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (default: the workload's own count; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 55-mer count of the same reads after the headline workload")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the random-access peak measurements")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -91,6 +91,8 @@ SIGNATURES = {
     "kmerco_batch_classify": (c_int, [c_void_p]),
     "kmerco_batch_schedule": (c_int, [c_void_p, c_int, c_int]),
     "kmerco_batch_info": (c_int, [c_void_p, c_void_p]),
+    "kmerco_peak_random_cas": (c_int, [c_uint64, c_uint64, c_int, POINTER(ctypes.c_double)]),
+    "kmerco_peak_random_read": (c_int, [c_uint64, c_uint64, c_int, POINTER(ctypes.c_double)]),
 }
 
 NOALLOC_MAX_KEYS = 1 << 28
@@ -282,6 +284,21 @@ def kmerco_batch_info(b: int) -> dict:
     info = kmerco_batch_info_t()
     _check(load().kmerco_batch_info(b, byref(info)), "kmerco_batch_info")
     return info.as_dict()
+
+
+def kmerco_peak_random_cas(nbytes: int, ops: int, device: int = -1) -> float:
+    """Random 64-bit load + compare-and-swap operations per second over a
+    buffer of nbytes (kmerco_peaks.h)."""
+    r = ctypes.c_double(0.0)
+    _check(load().kmerco_peak_random_cas(nbytes, ops, device, byref(r)), "kmerco_peak_random_cas")
+    return r.value
+
+
+def kmerco_peak_random_read(nbytes: int, ops: int, device: int = -1) -> float:
+    """Random 8-byte reads per second over a buffer of nbytes (kmerco_peaks.h)."""
+    r = ctypes.c_double(0.0)
+    _check(load().kmerco_peak_random_read(nbytes, ops, device, byref(r)), "kmerco_peak_random_read")
+    return r.value
 
 
 # ------------------------------------------------------------------ wrapper

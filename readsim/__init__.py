@@ -28,6 +28,8 @@ Illumina-like reads, both strands, substitution/indel errors, N calls):
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -44,6 +46,21 @@ class Stream:
 
     def raw(self, n: int) -> np.ndarray:
         return self._bg.random_raw(n).astype(np.uint64, copy=False)
+
+    def fork(self, skip: int) -> "Stream":
+        """A new stream positioned ``skip`` raw words after this one (which
+        does not move): it yields what this stream would after ``skip`` draws."""
+        s = Stream.__new__(Stream)
+        s._bg = np.random.PCG64()
+        s._bg.state = self._bg.state
+        if skip:
+            s._bg.advance(skip)
+        return s
+
+    def skip(self, n: int) -> None:
+        """Move past n raw words without drawing them."""
+        if n:
+            self._bg.advance(n)
 
     def uniform(self, n: int) -> np.ndarray:
         """Doubles in [0, 1): top 53 bits of each raw word."""
@@ -104,9 +121,14 @@ class ReadModel:
 
 
 def sample_reads(g: np.ndarray, model: ReadModel, stream: Stream,
-                 chunk: int = 200_000) -> tuple[np.ndarray, np.ndarray]:
-    """Sample reads from a circular genome ``g`` (base indices)."""
-    G = len(g)
+                 chunk: int = 200_000, threads: int | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """Sample reads from a circular genome ``g`` (base indices).
+
+    Reads are drawn in chunks of ``chunk`` reads.  Every chunk takes a fixed
+    number of raw words from the stream, so chunk c starts at a known stream
+    position and the chunks run on ``threads`` threads (default: the CPU
+    count) with the same result as one after another; the stream ends where
+    a sequential pass would leave it."""
     n = model.n_reads
     if isinstance(model.read_len, tuple):
         lo, hi = model.read_len
@@ -117,6 +139,32 @@ def sample_reads(g: np.ndarray, model: ReadModel, stream: Stream,
     np.cumsum(lens, out=offsets[1:])
     bases = np.empty(int(offsets[-1]), dtype=np.uint8)
     lmax = int(lens.max()) if n else 0
+    # raw words per read of a chunk: its start, lmax per-base words, the
+    # strand, lmax N-call uniforms
+    per_read = 1 + lmax + (1 if model.both_strands else 0) + (lmax if model.n_rate > 0 else 0)
+    starts = list(range(0, n, chunk))
+
+    def one(r0: int) -> None:
+        r1 = min(n, r0 + chunk)
+        _sample_chunk(g, model, lens[r0:r1].astype(np.int64), lmax,
+                      stream.fork(r0 * per_read), bases[int(offsets[r0]):int(offsets[r1])])
+
+    nt = threads if threads is not None else min(16, os.cpu_count() or 1)
+    if nt > 1 and len(starts) > 1:
+        with cf.ThreadPoolExecutor(min(nt, len(starts))) as ex:
+            list(ex.map(one, starts))
+    else:
+        for r0 in starts:
+            one(r0)
+    stream.skip(n * per_read)
+    return bases, offsets
+
+
+def _sample_chunk(g: np.ndarray, model: ReadModel, L: np.ndarray, lmax: int, stream: Stream,
+                  out: np.ndarray) -> None:
+    """Reads of lengths L (one chunk) into ``out``, drawing from ``stream``."""
+    G = len(g)
+    nr = len(L)
     # per-base draws come from one raw 64-bit word: bits 32..63 choose the
     # error type against integer thresholds, bits 0..15 the substitution
     # (1, 2 or 3 steps round A,C,G,T), bits 16..17 an inserted base
@@ -125,46 +173,40 @@ def sample_reads(g: np.ndarray, model: ReadModel, stream: Stream,
     t_del = np.uint64(int((model.sub + model.ins + model.dele) * 2 ** 32))
     indels = model.ins > 0 or model.dele > 0
     jj = np.arange(lmax, dtype=np.int64)[None, :]
-    for r0 in range(0, n, chunk):
-        r1 = min(n, r0 + chunk)
-        nr = r1 - r0
-        L = lens[r0:r1].astype(np.int64)
-        start = stream.integers(nr, G)
-        raw = stream.raw(nr * lmax).reshape(nr, lmax)
-        top = raw >> np.uint64(32)
-        is_sub = top < t_sub
-        if indels:
-            is_ins = (top >= t_sub) & (top < t_ins)
-            is_del = (top >= t_ins) & (top < t_del)
-            adv = np.where(is_ins, 0, np.where(is_del, 2, 1)).astype(np.int64)
-            before = np.cumsum(adv, axis=1) - adv
-            tidx = (start[:, None] + before + is_del.astype(np.int64)) % G
-        else:
-            tidx = (start[:, None] + jj) % G
-        codes = g[tidx]
-        if indels:
-            rnd = ((raw >> np.uint64(16)) & np.uint64(3)).astype(np.uint8)
-            codes = np.where(is_ins, rnd, codes)
-        shift = (((raw & np.uint64(0xFFFF)) * np.uint64(3)) >> np.uint64(16)).astype(np.uint8) + 1
-        codes = np.where(is_sub, (codes + shift) & 3, codes).astype(np.uint8)
-        if model.both_strands:
-            rev = stream.uniform(nr) < 0.5
-        else:
-            rev = np.zeros(nr, dtype=bool)
-        asc = ASCII[codes]
-        if model.n_rate > 0:
-            asc[stream.uniform(nr * lmax).reshape(nr, lmax) < model.n_rate] = ord("N")
-        # opposite strand: complement (A<->T, C<->G, N stays) and reverse each
-        # read within its own length
-        if rev.any():
-            src = np.where(rev[:, None], L[:, None] - 1 - jj, jj)
-            np.clip(src, 0, lmax - 1, out=src)
-            asc = np.take_along_axis(asc, src, axis=1)
-            asc = np.where(rev[:, None], _COMPLEMENT[asc], asc)
-        keep = jj < L[:, None]
-        o0, o1 = int(offsets[r0]), int(offsets[r1])
-        bases[o0:o1] = asc[keep]
-    return bases, offsets
+    start = stream.integers(nr, G)
+    raw = stream.raw(nr * lmax).reshape(nr, lmax)
+    top = raw >> np.uint64(32)
+    is_sub = top < t_sub
+    if indels:
+        is_ins = (top >= t_sub) & (top < t_ins)
+        is_del = (top >= t_ins) & (top < t_del)
+        adv = np.where(is_ins, 0, np.where(is_del, 2, 1)).astype(np.int64)
+        before = np.cumsum(adv, axis=1) - adv
+        tidx = (start[:, None] + before + is_del.astype(np.int64)) % G
+    else:
+        tidx = (start[:, None] + jj) % G
+    codes = g[tidx]
+    if indels:
+        rnd = ((raw >> np.uint64(16)) & np.uint64(3)).astype(np.uint8)
+        codes = np.where(is_ins, rnd, codes)
+    shift = (((raw & np.uint64(0xFFFF)) * np.uint64(3)) >> np.uint64(16)).astype(np.uint8) + 1
+    codes = np.where(is_sub, (codes + shift) & 3, codes).astype(np.uint8)
+    if model.both_strands:
+        rev = stream.uniform(nr) < 0.5
+    else:
+        rev = np.zeros(nr, dtype=bool)
+    asc = ASCII[codes]
+    if model.n_rate > 0:
+        asc[stream.uniform(nr * lmax).reshape(nr, lmax) < model.n_rate] = ord("N")
+    # opposite strand: complement (A<->T, C<->G, N stays) and reverse each
+    # read within its own length
+    if rev.any():
+        src = np.where(rev[:, None], L[:, None] - 1 - jj, jj)
+        np.clip(src, 0, lmax - 1, out=src)
+        asc = np.take_along_axis(asc, src, axis=1)
+        asc = np.where(rev[:, None], _COMPLEMENT[asc], asc)
+    keep = jj < L[:, None]
+    out[:] = asc[keep]
 
 
 _COMPLEMENT = np.arange(256, dtype=np.uint8)

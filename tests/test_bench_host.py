@@ -2,29 +2,49 @@
 import bench
 
 
-def test_roofline_counts_random_sector_bytes_per_update():
-    # 1.2e8 K-mers, k_h = 4: 256 B each in the random-sector model
-    r = bench.roofline_of_insert(120_000_000, 23_535_998, 4, 158_000_008, 6.0, 6658.6, None)
-    assert r["algorithmic_bytes_per_kmer"] == 256
-    assert r["algorithmic_bytes_per_launch"] == 120_000_000 * 256
-    assert abs(r["achieved"] - 120_000_000 * 256 / 0.006 / 1e9) < 1e-6
+def test_word_granular_bytes_are_the_headline():
+    # 1.2e8 K-mers, k_h = 4, one-word keys: 4 x 16 B of cell read-modify-write
+    # plus the key written and read once (16 B) per K-mer, plus the input
+    r = bench.roofline_of_insert(120_000_000, 4, 1, 158_000_008, 6.0, 6658.6, None)
+    assert r["algorithmic_bytes_per_kmer"] == 80
+    assert r["algorithmic_bytes_per_launch"] == 158_000_008 + 120_000_000 * 80
+    assert abs(r["achieved"] - r["algorithmic_bytes_per_launch"] / 0.006 / 1e9) < 1e-6
     assert abs(r["frac"] - r["achieved"] / 6658.6) < 1e-12
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] is None
 
 
-def test_word_granular_count():
-    r = bench.roofline_of_insert(1000, 200, 3, 5000, 1.0, 1000.0, 123.0)
-    wg = r["word_granular"]
-    assert wg["bytes_per_launch"] == 5000 + 1000 * (16 * 3 + 8) + 200 * 16
-    assert abs(wg["frac"] - wg["bytes_per_launch"] / 1e-3 / 1e9 / 1000.0) < 1e-12
+def test_two_word_keys_and_the_sector_model():
+    r = bench.roofline_of_insert(1000, 3, 2, 5000, 1.0, 1000.0, 123.0)
+    assert r["algorithmic_bytes_per_launch"] == 5000 + 1000 * (16 * 3 + 32)
+    sm = r["sector_model"]
+    assert sm["bytes_per_launch"] == 1000 * 64 * 3
+    assert abs(sm["frac"] - sm["bytes_per_launch"] / 1e-3 / 1e9 / 1000.0) < 1e-12
     assert r["traffic"] == 123.0 and r["avg_launch_ms"] == 1.0
+    assert abs(r["traffic_over_algorithmic"] - 123.0 / r["algorithmic_bytes_per_launch"]) < 1e-15
 
 
-def test_traffic_record_is_well_formed():
-    # one record line: the code hash it was taken on and the DRAM bytes of one call
-    lines = [l for l in open(bench.PROFILE_SUMMARY) if l.startswith("traffic_record")]
-    assert len(lines) == 1
-    kv = dict(p.split("=", 1) for p in lines[0].split()[1:])
-    assert len(kv["source_sha"]) == 16 and int(kv["source_sha"], 16) >= 0
-    assert float(kv["dram_bytes_per_launch"]) > 0
+def test_l2_atomic_view():
+    r = bench.l2_atomic_roofline(1_000_000, 3, 0.5, 64e9)
+    assert r["bound"] == "l2_atomic"
+    assert abs(r["achieved"] - 3e6 / 0.0005 / 1e9) < 1e-9
+    assert abs(r["frac"] - 3e6 / 0.0005 / 64e9) < 1e-12
+
+
+def test_host_cpu_reports_model_and_cores():
+    c = bench.host_cpu()
+    assert c["nproc"] >= 1 and isinstance(c["cpu_model"], str) and c["cpu_model"]
+
+
+def test_traffic_records_are_well_formed():
+    # one record line per summary: the code hash it was taken on and the
+    # DRAM bytes of one call
+    import os
+    for path in bench.PROFILE_SUMMARIES.values():
+        if not os.path.exists(path):
+            continue
+        lines = [l for l in open(path) if l.startswith("traffic_record")]
+        assert len(lines) == 1
+        kv = dict(p.split("=", 1) for p in lines[0].split()[1:])
+        assert len(kv["source_sha"]) == 16 and int(kv["source_sha"], 16) >= 0
+        assert float(kv["dram_bytes_per_launch"]) > 0
     assert len(bench.source_sha()) == 16
