@@ -174,12 +174,18 @@ def host_cpu() -> dict:
                     break
     except OSError:
         pass
-    if model is None:
+    if model is None:   # Arm hosts name the core in lscpu, not in /proc/cpuinfo
         try:
-            import platform
-            model = platform.processor() or platform.machine()
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
         except Exception:
-            model = "unknown"
+            pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine() or "unknown"
     return {"cpu_model": model, "nproc": os.cpu_count()}
 
 

@@ -59,6 +59,19 @@ extern "C" {
 
 typedef struct kmerco kmerco_t;
 
+/*
+ * Device allocator of a handle (kmerco_config_t.dev_alloc / dev_free), so
+ * that the library's device memory can come from the caller's own pool (a
+ * framework's caching allocator) instead of cudaMalloc.  alloc returns
+ * `bytes` of device memory of the handle's device, 16-byte aligned at
+ * least, or NULL; stream is the handle's cudaStream_t, on which the block is
+ * used.  free returns a block with the size it was allocated with; the
+ * library calls it only after the handle's device work has finished (it
+ * synchronises the handle's streams first).  ctx is passed through.
+ */
+typedef void *(*kmerco_alloc_fn)(void *ctx, size_t bytes, void *stream);
+typedef void (*kmerco_free_fn)(void *ctx, void *ptr, size_t bytes, void *stream);
+
 /* Options of kmerco_create_ex().  Zero-initialise, then set fields. */
 typedef struct {
     int k;                 /* K-mer length, 1..64 (Table 1) */
@@ -98,6 +111,20 @@ typedef struct {
                               the scratch memory (about 7 bytes per staged increment with the
                               counting apply: a 4-byte region code and a 2-byte slice code,
                               with headroom; about 10 with the compare-and-swap apply). */
+    uint32_t retry_limit;  /* bound of the device retry loops: compare-and-swap retries of one
+                              counter update (Algorithm 3's read-modify-write) and probes of one
+                              distinct-set insert.  0: 2^22 and 2^20.  A loop that reaches it
+                              stops, so the counts are incomplete, and the next classify or
+                              stats returns KMERCO_ETIMEOUT; reset clears the state.  Small
+                              values exist to exercise that path on contended input. */
+    uint64_t max_distinct; /* most distinct keys the handle's distinct list may hold; 0: no
+                              limit (it grows with the input).  Keys beyond it are left out of
+                              the list and the next classify or stats returns KMERCO_ENOMEM;
+                              reset clears the state. */
+    kmerco_alloc_fn dev_alloc;  /* device allocator of every buffer of the handle; both NULL:
+                                   cudaMalloc / cudaFree.  Only one of the two set: EINVAL. */
+    kmerco_free_fn dev_free;
+    void *alloc_ctx;       /* passed to dev_alloc and dev_free */
 } kmerco_config_t;
 
 /* Running totals and results of one handle (kmerco_stats). */
@@ -144,6 +171,20 @@ int kmerco_create(int k, uint64_t m, int counter_bits, int nhash, uint32_t thres
  */
 int kmerco_paper_dims(uint64_t n, double fpp, uint64_t *dim_x, uint64_t *dim_y);
 
+/*
+ * Device bytes a handle with options *cfg holds at most after one
+ * kmerco_insert of nreads reads (nbytes bases, `windows` windows: the sum of
+ * max(0, len - K + 1), or the whole-file count) and one kmerco_classify:
+ * the countBF, a distinct set and list sized for every window being a new
+ * key, the increment-code buffers of the update design the call would take,
+ * the classification buffers for that many distinct keys, and with
+ * host_inputs != 0 the staging copy of the reads.  This is the figure a
+ * scheduler can admit a job by, and give the handle as its hbm_budget.
+ * No device work; cfg->dev_alloc must be NULL.  Errors: EINVAL.
+ */
+int kmerco_estimate_bytes(const kmerco_config_t *cfg, uint64_t nreads, uint64_t nbytes,
+                          uint64_t windows, int host_inputs, uint64_t *bytes);
+
 /* As kmerco_create() with every option of kmerco_config_t. */
 int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out);
 
@@ -164,8 +205,12 @@ void kmerco_destroy(kmerco_t *h);
  * counter of kmerco_config_t.dim_x) is incremented unless it already holds
  * 2^alpha - 1.  The key also joins the handle's distinct-key set.
  * Calls accumulate; order of reads and calls does not change any result.
- * Asynchronous on the handle's stream, except that device-resident offsets
- * are read back once to size internal buffers.
+ * Asynchronous on the handle's stream.  The buffers are sized from the
+ * call's window count: host offsets of up to 2^22 reads are checked and
+ * summed on the host, so the call does not wait for the device; device
+ * offsets, and host offsets of more reads, are summed by a kernel whose
+ * result the call waits for.  A call that has to grow the distinct set
+ * also waits for the keys already held.
  * Errors: EINVAL (NULL pointer with nreads > 0, nreads >= 2^32 - 1,
  * decreasing offsets); ENOMEM; ECUDA.
  */

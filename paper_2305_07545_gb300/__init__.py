@@ -24,12 +24,42 @@ LIB_PATH = os.path.join(_HERE, "libkmerco.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ESIZE = range(7)
 
 
+# kmerco_alloc_fn / kmerco_free_fn: a handle's device allocator
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_void_p, ctypes.c_size_t, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p, ctypes.c_size_t, c_void_p)
+
+
 class kmerco_config_t(ctypes.Structure):
     _fields_ = [("k", c_int), ("m", c_uint64), ("counter_bits", c_int), ("nhash", c_int),
                 ("threshold", c_uint32), ("forward_only", c_int), ("stream", c_void_p),
                 ("hbm_budget", c_uint64), ("device", c_int), ("update_mode", c_int),
                 ("dim_x", c_uint64), ("dim_y", c_uint64), ("canonical_hash", c_int),
-                ("whole_file", c_int), ("pass_codes", c_uint64)]
+                ("whole_file", c_int), ("pass_codes", c_uint64), ("retry_limit", c_uint32),
+                ("max_distinct", c_uint64), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_ctx", c_void_p)]
+
+
+class TorchAllocator:
+    """Device memory of a handle from torch's caching allocator (the
+    handle's dev_alloc / dev_free callbacks), so that the library's buffers
+    count in torch.cuda.memory_allocated() and come from torch's pool."""
+
+    def __init__(self, device: int | None = None):
+        import torch
+        self.device = torch.cuda.current_device() if device is None else device
+
+        def _alloc(ctx, nbytes, stream):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                          int(stream or 0))
+            except Exception:   # out of memory: the library reports ENOMEM
+                return None
+
+        def _free(ctx, ptr, nbytes, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc = ALLOC_FN(_alloc)   # kept alive with the handle
+        self.free = FREE_FN(_free)
 
 
 class kmerco_stats_t(ctypes.Structure):
@@ -91,6 +121,8 @@ SIGNATURES = {
     "kmerco_batch_classify": (c_int, [c_void_p]),
     "kmerco_batch_schedule": (c_int, [c_void_p, c_int, c_int]),
     "kmerco_batch_info": (c_int, [c_void_p, c_void_p]),
+    "kmerco_estimate_bytes": (c_int, [POINTER(kmerco_config_t), c_uint64, c_uint64, c_uint64, c_int,
+                                      _u64p]),
     "kmerco_peak_random_cas": (c_int, [c_uint64, c_uint64, c_int, POINTER(ctypes.c_double)]),
     "kmerco_peak_random_read": (c_int, [c_uint64, c_uint64, c_int, POINTER(ctypes.c_double)]),
 }
@@ -160,14 +192,40 @@ def kmerco_create_ex(k: int, m: int, counter_bits: int, nhash: int, threshold: i
                      forward_only: bool = False, stream: int | None = None,
                      hbm_budget: int = 0, device: int = -1, update_mode: int = 0,
                      dims: tuple[int, int] | None = None, pass_codes: int = 0,
-                     canonical_hash: bool = False, whole_file: bool = False) -> int:
+                     canonical_hash: bool = False, whole_file: bool = False,
+                     retry_limit: int = 0, max_distinct: int = 0,
+                     allocator: "TorchAllocator | None" = None) -> int:
     dx, dy = dims if dims is not None else (0, 0)
     cfg = kmerco_config_t(k, m, counter_bits, nhash, threshold, int(forward_only),
                           stream or None, hbm_budget, device, update_mode, dx, dy,
-                          int(canonical_hash), int(whole_file), pass_codes)
+                          int(canonical_hash), int(whole_file), pass_codes, retry_limit,
+                          max_distinct)
+    if allocator is not None:
+        cfg.dev_alloc = allocator.alloc
+        cfg.dev_free = allocator.free
     h = c_void_p()
     _check(load().kmerco_create_ex(byref(cfg), byref(h)), "kmerco_create_ex")
     return h.value
+
+
+def kmerco_estimate_bytes(k: int, m: int, counter_bits: int, nhash: int, threshold: int,
+                          nreads: int, nbytes: int, windows: int, host_inputs: bool = True,
+                          **options) -> int:
+    """Most device bytes a handle holds after one insert of these reads and
+    one classify (kmerco.h); options as kmerco_create_ex (no allocator)."""
+    dims = options.pop("dims", None)
+    dx, dy = dims if dims is not None else (0, 0)
+    cfg = kmerco_config_t(k, m, counter_bits, nhash, threshold, int(options.pop("forward_only", 0)),
+                          None, options.pop("hbm_budget", 0), -1, options.pop("update_mode", 0),
+                          dx, dy, int(options.pop("canonical_hash", 0)),
+                          int(options.pop("whole_file", 0)), options.pop("pass_codes", 0), 0,
+                          options.pop("max_distinct", 0))
+    if options:
+        raise TypeError(f"unknown options {sorted(options)}")
+    out = c_uint64(0)
+    _check(load().kmerco_estimate_bytes(byref(cfg), nreads, nbytes, windows, int(host_inputs),
+                                        byref(out)), "kmerco_estimate_bytes")
+    return out.value
 
 
 def kmerco_paper_dims(n: int, fpp: float = 0.001) -> tuple[int, int]:
@@ -313,18 +371,26 @@ class CountBF:
                  threshold: int = 3, forward_only: bool = False, stream: int | None = None,
                  hbm_budget: int = 0, device: int = -1, update_mode: int = UPDATE_AUTO,
                  dims: tuple[int, int] | None = None, pass_codes: int = 0,
-                 canonical_hash: bool = False, whole_file: bool = False):
+                 canonical_hash: bool = False, whole_file: bool = False,
+                 retry_limit: int = 0, max_distinct: int = 0, allocator=None):
         """``dims = (X, Y)`` makes a two-dimensional countBF of X x Y cells
-        (Algorithm 3's addressing; ``m`` is then ignored)."""
+        (Algorithm 3's addressing; ``m`` is then ignored).  ``allocator="torch"``
+        (or a :class:`TorchAllocator`) takes the handle's device memory from
+        torch's caching allocator."""
+        if allocator == "torch":
+            allocator = TorchAllocator(None if device < 0 else device)
+        self.allocator = allocator   # its callbacks must outlive the handle
         self.k = k
         self.kw = 1 if k <= 32 else 2
         self.params = dict(k=k, m=m, counter_bits=counter_bits, nhash=nhash,
                            threshold=threshold, forward_only=bool(forward_only),
                            dims=tuple(dims) if dims is not None else None,
                            canonical_hash=bool(canonical_hash), whole_file=bool(whole_file))
+        self.h = None
         self.h = kmerco_create_ex(k, m, counter_bits, nhash, threshold, forward_only, stream,
                                   hbm_budget, device, update_mode, dims, pass_codes,
-                                  canonical_hash, whole_file)
+                                  canonical_hash, whole_file, retry_limit, max_distinct,
+                                  allocator)
 
     def save(self, path: str) -> None:
         """Write the countBF, its distinct keys and its parameters to an

@@ -18,6 +18,10 @@
 using namespace countbf;
 
 constexpr int kCopyPieces = 8;   // pieces of a host input copied while earlier ones are inserted
+// Host offsets of up to this many reads are checked and summed on the host
+// (a few milliseconds at most), so the insert does not wait for the device;
+// larger ones are copied and summed by a kernel, which the call waits for.
+constexpr uint64_t kHostBoundReads = 1ull << 22;
 
 struct kmerco {
     int K, kw, alpha, eta, nhash, canonical;   // canonical: 0 forward, 1 lexicographic, 2 hash
@@ -30,6 +34,10 @@ struct kmerco {
     uint64_t pass_codes;     // increments staged per partitioned pass
     int grid_atomic, grid_part, grid_wide;   // insert grids: atomic, partitioned, wide partitioned
     uint64_t budget, used;
+    uint64_t max_distinct;   // cap of the distinct list; 0: none
+    kmerco_alloc_fn alloc_fn;   // caller's device allocator, or NULL for cudaMalloc
+    kmerco_free_fn free_fn;
+    void *alloc_ctx;
     Geometry G;
     DevCounters *ctr;        // device
     DevCounters *ctr_host;   // pinned mirror
@@ -113,23 +121,55 @@ int cuda_status(cudaError_t e) {
         if (r_ != KMERCO_OK) return r_;  \
     } while (0)
 
-int dev_alloc(kmerco_t *h, void **p, uint64_t bytes) {
+// Device memory from the handle's allocator: the caller's callbacks when
+// it gave them, else cudaMalloc / cudaFree.
+int raw_alloc(const kmerco_t *h, void **p, uint64_t bytes) {
     *p = nullptr;
-    if (bytes == 0) bytes = 16;
-    if (h->budget && h->used + bytes > h->budget) return KMERCO_ENOMEM;
+    if (h->alloc_fn) {
+        void *q = h->alloc_fn(h->alloc_ctx, (size_t)bytes, (void *)h->stream);
+        if (!q) return KMERCO_ENOMEM;
+        if ((uintptr_t)q & 15) {   // vector loads need 16-byte alignment
+            h->free_fn(h->alloc_ctx, q, (size_t)bytes, (void *)h->stream);
+            return KMERCO_EINVAL;
+        }
+        *p = q;
+        return KMERCO_OK;
+    }
     if (cudaMalloc(p, bytes) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return KMERCO_ENOMEM;
     }
+    return KMERCO_OK;
+}
+
+void raw_free(const kmerco_t *h, void *p, uint64_t bytes) {
+    if (!p) return;
+    if (h->free_fn) {
+        // the block goes back to the caller's pool, which may hand it out
+        // at once: the work that used it must have finished
+        cudaStreamSynchronize(h->stream);
+        if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+        h->free_fn(h->alloc_ctx, p, (size_t)bytes, (void *)h->stream);
+        return;
+    }
+    cudaFree(p);
+}
+
+int dev_alloc(kmerco_t *h, void **p, uint64_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (h->budget && h->used + bytes > h->budget) return KMERCO_ENOMEM;
+    KM_TRY(raw_alloc(h, p, bytes));
     h->used += bytes;
     return KMERCO_OK;
 }
 
 void dev_free(kmerco_t *h, void *p, uint64_t bytes) {
     if (!p) return;
-    cudaFree(p);
-    h->used -= bytes ? bytes : 16;
+    if (bytes == 0) bytes = 16;
+    raw_free(h, p, bytes);
+    h->used -= bytes;
 }
 
 // Make *p hold at least `need` elements of `elem` bytes (contents dropped).
@@ -177,14 +217,23 @@ int ensure_set_capacity(kmerco_t *h, uint64_t add) {
         h->d_ub = need;
         return KMERCO_OK;
     }
-    KM_TRY(read_counters(h));
-    const uint64_t D = h->ctr_host->distinct;
+    uint64_t D = 0;   // nothing inserted since create or reset: no keys to read back
+    if (h->d_ub) {
+        KM_TRY(read_counters(h));
+        D = h->ctr_host->distinct;
+    }
     need = D + add;
-    if (need > h->dlist_cap) {
-        uint64_t want = need > h->dlist_cap + h->dlist_cap / 2 ? need : h->dlist_cap + h->dlist_cap / 2;
+    // with a cap on the distinct list, keys beyond it are dropped on the
+    // device (the list-full error) instead of growing the list
+    const uint64_t list_need = h->max_distinct && need > h->max_distinct ? h->max_distinct : need;
+    if (list_need > h->dlist_cap) {
+        uint64_t want = list_need > h->dlist_cap + h->dlist_cap / 2 ? list_need
+                                                                    : h->dlist_cap + h->dlist_cap / 2;
+        if (h->max_distinct && want > h->max_distinct) want = h->max_distinct;
         void *q;
         KM_TRY(dev_alloc(h, &q, want * h->kw * 8));
-        if (D) KM_CUDA(cudaMemcpyAsync(q, h->dlist, D * h->kw * 8, cudaMemcpyDeviceToDevice, h->stream));
+        if (D) KM_CUDA(cudaMemcpyAsync(q, h->dlist, (D < h->dlist_cap ? D : h->dlist_cap) * h->kw * 8,
+                                       cudaMemcpyDeviceToDevice, h->stream));
         KM_CUDA(cudaStreamSynchronize(h->stream));
         dev_free(h, h->dlist, h->dlist_cap * h->kw * 8);
         h->dlist = (uint64_t *)q;
@@ -197,7 +246,8 @@ int ensure_set_capacity(kmerco_t *h, uint64_t add) {
         void *q;
         KM_TRY(dev_alloc(h, &q, want * h->kw * 8));
         KM_CUDA(cudaMemsetAsync(q, 0xFF, want * h->kw * 8, h->stream));
-        KM_CUDA(launch_reinsert(h->dlist, D, h->kw, (uint64_t *)q, want, nullptr, 0, h->ctr,
+        KM_CUDA(launch_reinsert(h->dlist, D < h->dlist_cap ? D : h->dlist_cap, h->kw,
+                                (uint64_t *)q, want, nullptr, 0, h->ctr, h->G.probe_limit,
                                 h->stream));
         h->launches += D ? 1 : 0;
         KM_CUDA(cudaStreamSynchronize(h->stream));
@@ -228,6 +278,7 @@ int validate(const kmerco_config_t *c) {
     if (c->whole_file != 0 && c->whole_file != 1) return KMERCO_EINVAL;
     if (c->update_mode < 0 || c->update_mode > 2) return KMERCO_EINVAL;
     if (c->pass_codes > kMaxBatchCodes) return KMERCO_EINVAL;
+    if ((c->dev_alloc == nullptr) != (c->dev_free == nullptr)) return KMERCO_EINVAL;
     if (c->update_mode == 2) {
         const uint64_t eta = 64 / (uint64_t)c->counter_bits;
         const uint64_t words = c->dim_x ? c->dim_x * c->dim_y : (c->m + eta - 1) / eta;
@@ -503,6 +554,52 @@ int kmerco_paper_dims(uint64_t n, double fpp, uint64_t *dim_x, uint64_t *dim_y) 
     return KMERCO_OK;
 }
 
+int kmerco_estimate_bytes(const kmerco_config_t *cfg, uint64_t nreads, uint64_t nbytes,
+                          uint64_t windows, int host_inputs, uint64_t *bytes) {
+    if (!bytes) return KMERCO_EINVAL;
+    KM_TRY(validate(cfg));
+    if (cfg->dev_alloc) return KMERCO_EINVAL;   // plain sizes only; no handle is made
+    // a handle's sizing state without any device object
+    kmerco_t t;
+    memset(&t, 0, sizeof(t));
+    t.K = cfg->k;
+    t.kw = cfg->k <= 32 ? 1 : 2;
+    t.alpha = cfg->counter_bits;
+    t.eta = 64 / cfg->counter_bits;
+    t.nhash = cfg->nhash;
+    t.update_mode = cfg->update_mode;
+    t.pass_codes = cfg->pass_codes ? cfg->pass_codes : kMaxBatchCodes;
+    t.G = make_geometry((cfg->m + (uint64_t)t.eta - 1) / (uint64_t)t.eta, cfg->dim_x, cfg->dim_y,
+                        t.alpha, t.nhash);
+    const uint64_t kw = (uint64_t)t.kw;
+    // ensure(): need + need / 4 + 64 elements
+    auto grown = [](uint64_t need, uint64_t elem) { return (need + need / 4 + 64) * elem; };
+    uint64_t b = t.G.words * 8 + sizeof(DevCounters);
+    if (host_inputs) b += grown(nbytes, 1) + grown(nreads + 1, 8);
+    if (windows) {
+        // distinct list and set for every window being a new key
+        uint64_t list = windows;
+        if (cfg->max_distinct && list > cfg->max_distinct) list = cfg->max_distinct;
+        b += list * kw * 8 + std::max<uint64_t>(2 * windows, 1024) * kw * 8;
+        const PartPlan pp = plan_partition(&t, windows, nbytes);
+        if (pp.part) {
+            b += grown(pp.coarse_words(), 4) + grown(pp.ctr_words(), 8);
+            if (pp.repart) b += grown(pp.fine_words(), 4);
+        }
+        const uint64_t chunk = pp.part ? kPartChunk : kChunk;
+        b += grown((nbytes + chunk - 1) / chunk, 4);
+        // classification of at most `windows` distinct keys
+        const uint64_t D = windows;
+        b += 2 * grown(D * kw, 8) + grown(D, 4) + grown(D * kw, 8) +
+             grown(sort_scratch_words(D, kw), 4) + grown(split_scratch_words(D), 8);
+        if (kw == 1 && 2 * t.K >= kHistBits + 8 && D > 65536)   // the bucket sort may run
+            b += grown(kBucketHostWords + kHistBins, 8) +
+                 grown(bucket_hist_blocks(D) * kHistBins, 2);
+    }
+    *bytes = b;
+    return KMERCO_OK;
+}
+
 int kmerco_create(int k, uint64_t m, int counter_bits, int nhash, uint32_t threshold,
                   kmerco_t **out) {
     kmerco_config_t c;
@@ -532,6 +629,10 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
     h->canonical = cfg->forward_only ? 0 : cfg->canonical_hash ? 2 : 1;
     h->whole_file = cfg->whole_file;
     h->budget = cfg->hbm_budget;
+    h->max_distinct = cfg->max_distinct;
+    h->alloc_fn = cfg->dev_alloc;
+    h->free_fn = cfg->dev_free;
+    h->alloc_ctx = cfg->alloc_ctx;
     if (cfg->device >= 0) {
         h->device = cfg->device;
     } else if (cudaGetDevice(&h->device) != cudaSuccess) {
@@ -566,6 +667,7 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
         const uint64_t eta = (uint64_t)h->eta;
         h->G = make_geometry((cfg->m + eta - 1) / eta, cfg->dim_x, cfg->dim_y, h->alpha,
                              h->nhash);
+        if (cfg->retry_limit) h->G.cas_limit = h->G.probe_limit = cfg->retry_limit;
         Geometry &G = h->G;
         void *p;
         if ((status = dev_alloc(h, &p, G.words * 8))) break;
@@ -671,15 +773,26 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
                                 h->stream));
         d_off = h->in_offsets;
     }
-    KM_CUDA(cudaMemsetAsync(&h->ctr->bound, 0, sizeof(h->ctr->bound), h->stream));
-    KM_CUDA(cudaMemsetAsync(&h->ctr->bad_offsets, 0, sizeof(h->ctr->bad_offsets), h->stream));
-    KM_CUDA(launch_window_bound(d_off, nreads, K, h->ctr, h->stream));
-    h->launches += 1;
-    KM_TRY(read_counters(h));
-    if (h->ctr_host->bad_offsets) return KMERCO_EINVAL;
-    first = h->ctr_host->first;
-    last = h->ctr_host->last;
-    bound = h->ctr_host->bound;
+    if (host_offsets && nreads <= kHostBoundReads) {
+        // summed on the host: the call does not wait for the device
+        first = offsets[0];
+        last = offsets[nreads];
+        for (uint64_t r = 0; r < nreads; ++r) {
+            const uint64_t s = offsets[r], e = offsets[r + 1];
+            if (e < s) return KMERCO_EINVAL;
+            if (e - s >= (uint64_t)K) bound += e - s - K + 1;
+        }
+    } else {
+        KM_CUDA(cudaMemsetAsync(&h->ctr->bound, 0, sizeof(h->ctr->bound), h->stream));
+        KM_CUDA(cudaMemsetAsync(&h->ctr->bad_offsets, 0, sizeof(h->ctr->bad_offsets), h->stream));
+        KM_CUDA(launch_window_bound(d_off, nreads, K, h->ctr, h->stream));
+        h->launches += 1;
+        KM_TRY(read_counters(h));
+        if (h->ctr_host->bad_offsets) return KMERCO_EINVAL;
+        first = h->ctr_host->first;
+        last = h->ctr_host->last;
+        bound = h->ctr_host->bound;
+    }
     if (h->whole_file)   // the reads are one sequence of last - first bases
         bound = last - first >= (uint64_t)K ? last - first - K + 1 : 0;
     const uint64_t nbytes = last - first;
@@ -914,7 +1027,7 @@ int kmerco_add_distinct(kmerco_t *h, const uint64_t *keys, uint64_t n) {
     }
     KM_TRY(ensure_set_capacity(h, n));
     KM_CUDA(launch_reinsert(d_keys, n, h->kw, h->table, h->cap, h->dlist, h->dlist_cap, h->ctr,
-                            h->stream));
+                            h->G.probe_limit, h->stream));
     h->launches += 1;
     KM_TRY(read_counters(h));
     KM_TRY(device_error_status(h->ctr_host->error));
@@ -1009,7 +1122,7 @@ int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
     KM_TRY(ensure_set_capacity(dst, sc.distinct));
     KM_CUDA(launch_merge(dst->G.cells, src->G.cells, dst->G, dst->stream));
     KM_CUDA(launch_reinsert(src->dlist, sc.distinct, dst->kw, dst->table, dst->cap, dst->dlist,
-                            dst->dlist_cap, dst->ctr, dst->stream));
+                            dst->dlist_cap, dst->ctr, dst->G.probe_limit, dst->stream));
     dst->launches += sc.distinct ? 2 : 1;
     KM_TRY(read_counters(dst));
     DevCounters dc = *dst->ctr_host;
@@ -1169,13 +1282,13 @@ bool batch_alloc_scratch(kmerco_batch *b) {
         const uint64_t elem[3] = {4, 4, 8};
         for (int q = 0; q < 3; ++q) {
             if (b->buf_words[k][q] >= need[q]) continue;
-            cudaFree(*ptrs[q]);
+            if (*ptrs[q]) {
+                cudaStreamSynchronize(b->aux[k]);
+                raw_free(b->h[0], *ptrs[q], b->buf_words[k][q] * elem[q]);
+            }
             *ptrs[q] = nullptr;
             b->buf_words[k][q] = 0;
-            if (cudaMalloc(ptrs[q], need[q] * elem[q]) != cudaSuccess) {
-                cudaGetLastError();
-                return false;
-            }
+            if (raw_alloc(b->h[0], ptrs[q], need[q] * elem[q]) != KMERCO_OK) return false;
             b->buf_words[k][q] = need[q];
         }
     }
@@ -1255,11 +1368,12 @@ int kmerco_batch_create(kmerco_t *const *handles, int n, kmerco_batch_t **out) {
     if (b->sms <= 0) b->sms = 1;
     const int mx = insert_batch_blocks_per_sm(b->kw, kChunk);
     if (b->bpm > mx) b->bpm = mx;
-    bool ok = cudaMalloc((void **)&b->d_args, n * sizeof(InsertArgs)) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_chunk_end, n * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_bound, (size_t)n * kBoundOutWords * 8) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_offs, n * sizeof(uint64_t *)) == cudaSuccess &&
-              cudaMalloc((void **)&b->d_nreads, n * sizeof(uint64_t)) == cudaSuccess &&
+    const kmerco_t *h0 = handles[0];   // the batch's small arrays come from its allocator
+    bool ok = raw_alloc(h0, (void **)&b->d_args, n * sizeof(InsertArgs)) == KMERCO_OK &&
+              raw_alloc(h0, (void **)&b->d_chunk_end, n * sizeof(unsigned long long)) == KMERCO_OK &&
+              raw_alloc(h0, (void **)&b->d_bound, (size_t)n * kBoundOutWords * 8) == KMERCO_OK &&
+              raw_alloc(h0, (void **)&b->d_offs, n * sizeof(uint64_t *)) == KMERCO_OK &&
+              raw_alloc(h0, (void **)&b->d_nreads, n * sizeof(uint64_t)) == KMERCO_OK &&
               cudaEventCreate(&b->ev[0]) == cudaSuccess && cudaEventCreate(&b->ev[1]) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -1283,17 +1397,20 @@ void kmerco_batch_destroy(kmerco_batch_t *b) {
             cudaGraphExecDestroy(b->cls_exec);
             cudaGraphDestroy(b->cls_graph);
         }
-        cudaFree(b->d_args);
-        cudaFree(b->d_chunk_end);
-        cudaFree(b->d_bound);
-        cudaFree(b->d_offs);
-        cudaFree(b->d_nreads);
+        const kmerco_t *h0 = b->h[0];
+        const size_t n = (size_t)b->n;
+        raw_free(h0, b->d_args, n * sizeof(InsertArgs));
+        raw_free(h0, b->d_chunk_end, n * sizeof(unsigned long long));
+        raw_free(h0, b->d_bound, n * kBoundOutWords * 8);
+        raw_free(h0, b->d_offs, n * sizeof(uint64_t *));
+        raw_free(h0, b->d_nreads, n * sizeof(uint64_t));
         for (int i = 0; i < 2; ++i)
             if (b->ev[i]) cudaEventDestroy(b->ev[i]);
         for (int k = 0; k < kBatchStreams; ++k) {
-            cudaFree(b->bufs[k].coarse);
-            cudaFree(b->bufs[k].fine);
-            cudaFree(b->bufs[k].ctr);
+            if (b->aux[k]) cudaStreamSynchronize(b->aux[k]);
+            raw_free(h0, b->bufs[k].coarse, b->buf_words[k][0] * 4);
+            raw_free(h0, b->bufs[k].fine, b->buf_words[k][1] * 4);
+            raw_free(h0, b->bufs[k].ctr, b->buf_words[k][2] * 8);
             if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
             if (b->join[k]) cudaEventDestroy(b->join[k]);
         }

@@ -116,7 +116,8 @@ __device__ __forceinline__ void cas128(uint64_t *addr, uint64_t cmp_lo, uint64_t
 // (Algorithm 3: extract, add one unless at 2^alpha - 1, write back).  `old`
 // is a recent read of the cell; a failed CAS refreshes it.
 __device__ __forceinline__ void sat_increment(uint64_t *cells, uint64_t c, unsigned shift,
-                                              uint64_t maxc, uint64_t old, unsigned *err) {
+                                              uint64_t maxc, uint64_t old, uint32_t limit,
+                                              unsigned *err) {
     const uint64_t inc = 1ull << shift;
     for (uint32_t it = 0;; ++it) {
         if (((old >> shift) & maxc) == maxc) return;   // saturated: stays at the maximum
@@ -124,7 +125,7 @@ __device__ __forceinline__ void sat_increment(uint64_t *cells, uint64_t c, unsig
                                   (unsigned long long)(old + inc));
         if (prev == old) return;
         old = prev;
-        if (it >= kCasLimit) {
+        if (it >= limit) {
             atomicOr(err, kErrCasLimit);
             return;
         }
@@ -136,8 +137,9 @@ __device__ __forceinline__ void sat_increment(uint64_t *cells, uint64_t c, unsig
 // (kEmptyKey - 1 when none was loaded, a value no key or empty slot has).
 template <int KW>
 __device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64_t th,
-                                           uint64_t klo, uint64_t khi, unsigned *err,
-                                           uint64_t pol, uint64_t first = kEmptyKey - 1) {
+                                           uint64_t klo, uint64_t khi, uint32_t limit,
+                                           unsigned *err, uint64_t pol,
+                                           uint64_t first = kEmptyKey - 1) {
     uint64_t slot = __umul64hi(th, cap);
     for (uint32_t it = 0;; ++it) {
         if (KW == 1) {
@@ -158,7 +160,7 @@ __device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64
             if (olo == klo && ohi == khi) return false;
         }
         if (++slot == cap) slot = 0;
-        if (it >= kProbeLimit) {
+        if (it >= limit) {
             atomicOr(err, kErrProbeLimit);
             return false;
         }
@@ -435,13 +437,14 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (need[j] && prev[j] != cur[j])
-                    sat_increment(G.cells, cell[j], sh[j], G.maxc, prev[j], &a.ctr->error);
+                    sat_increment(G.cells, cell[j], sh[j], G.maxc, prev[j], G.cas_limit,
+                                  &a.ctr->error);
         }
 
         bool isnew = false;
         if (active)
-            isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, &a.ctr->error,
-                                   pol_stream, table_first);
+            isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, G.probe_limit,
+                                   &a.ctr->error, pol_stream, table_first);
         const unsigned bal = __ballot_sync(0xffffffffu, isnew);
         unsigned base = 0;
         if (lane == 0 && bal) base = atomicAdd(&S.nfresh, (unsigned)__popc(bal));
@@ -518,7 +521,7 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
                     const uint64_t cell = ((uint64_t)bin << a.coarse_shift) | (code >> 6);
                     const unsigned shift = (code & 63u) * (unsigned)G.alpha;
                     sat_increment(G.cells, cell, shift, G.maxc, load_cg(G.cells + cell),
-                                  &a.ctr->error);
+                                  G.cas_limit, &a.ctr->error);
                 }
             }
         }
@@ -703,7 +706,8 @@ __global__ void first_read_batch_kernel(const InsertArgs *args, const unsigned l
 // handle's keys).  With dlist != nullptr keys new to the set are appended.
 template <int KW>
 __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *table, uint64_t cap,
-                                uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr) {
+                                uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
+                                uint32_t probe_limit) {
     const int lane = threadIdx.x & 31;
     for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull; i0 < n;
          i0 += (uint64_t)gridDim.x * blockDim.x) {
@@ -718,7 +722,8 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
                 murmur8(premix8(klo), 0, h1, h2);
             else
                 murmur16(klo, khi, 0, h1, h2);
-            isnew = set_insert<KW>(table, cap, h2, klo, khi, &ctr->error, policy_stream());
+            isnew = set_insert<KW>(table, cap, h2, klo, khi, probe_limit, &ctr->error,
+                                   policy_stream());
         }
         if (dlist) {
             const unsigned bal = __ballot_sync(0xffffffffu, isnew);
@@ -870,7 +875,7 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
         } else {
             const uint64_t cell = ((uint64_t)b << p.coarse_shift) | word;
             sat_increment(p.G.cells, cell, (code & 63u) * (unsigned)p.G.alpha, p.G.maxc,
-                          load_cg(p.G.cells + cell), &p.ctr->error);
+                          load_cg(p.G.cells + cell), p.G.cas_limit, &p.ctr->error);
         }
     }
 }
@@ -927,7 +932,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
                 const unsigned long long prev = atomicCAS(cells_s + w, old, old + (1ull << shift));
                 if (prev == old) break;
                 old = prev;
-                if (it >= kCasLimit) {
+                if (it >= p.G.cas_limit) {
                     atomicOr(&p.ctr->error, kErrCasLimit);
                     break;
                 }
@@ -1168,14 +1173,16 @@ cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s) {
 
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,
                             uint64_t cap, uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
-                            cudaStream_t s) {
+                            uint32_t probe_limit, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     uint64_t blocks = (n + 255) / 256;
     if (blocks > 65536) blocks = 65536;
     if (kw == 1)
-        reinsert_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr);
+        reinsert_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr,
+                                                             probe_limit);
     else
-        reinsert_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr);
+        reinsert_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr,
+                                                             probe_limit);
     return cudaGetLastError();
 }
 

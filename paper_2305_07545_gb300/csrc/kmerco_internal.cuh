@@ -76,6 +76,8 @@ struct Geometry {
     int eta;
     int eta_log2;        // log2(eta) when eta is a power of two, else -1
     int nhash;
+    uint32_t cas_limit;    // retries of one counter update before it gives up
+    uint32_t probe_limit;  // probes of one distinct-set insert before it gives up
 };
 
 // Geometry of a countBF of `words` cells (flat: dim_x == 0) or of
@@ -100,6 +102,8 @@ inline Geometry make_geometry(uint64_t words, uint64_t dim_x, uint64_t dim_y, in
     G.mag_x = dim_x ? ~0ull / dim_x : 0;
     G.mag_y = dim_x ? ~0ull / dim_y : 0;
     G.mag_eta = ~0ull / (uint64_t)G.eta;
+    G.cas_limit = kCasLimit;
+    G.probe_limit = kProbeLimit;
     return G;
 }
 
@@ -322,7 +326,7 @@ cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_
 // set are appended to it (ctr->distinct counts them).
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,
                             uint64_t cap, uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
-                            cudaStream_t s);
+                            uint32_t probe_limit, cudaStream_t s);
 
 // Radix sort of n keys of kw words (1 or 2) on their low `bits` bits.  The
 // sorted keys end in *result, which is one of in, alt0 or alt1; in is left

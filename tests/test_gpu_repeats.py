@@ -71,16 +71,23 @@ def test_prefix_at_full_geometry_in_several_passes(K):
 
 
 def test_more_than_2_to_the_28_distinct_keys():
-    # 2^28 + 2^20 one-word keys (31-mers), a third of them drawn twice and a
-    # block of them sharing their top 20 bits, through kmerco_add_distinct
-    # (duplicates are dropped by the distinct set) and a classification
-    # against a countBF of random cells
+    # 2^28 + 2^22 distinct one-word keys (31-mers) built ascending from
+    # random gaps, so the sorted distinct list is known without a sort: one
+    # block of 2^20 keys has gaps of 1..16 (keys sharing their top bits), the
+    # rest gaps below 2^33.  They go in through kmerco_add_distinct in a
+    # strided order with a quarter of them a second time (dropped by the
+    # distinct set), then are classified against a countBF of random cells.
     K, m, alpha, nhash, tau = 31, 1 << 30, 4, 4, 3
-    n = (1 << 28) + (1 << 20)
+    n = (1 << 28) + (1 << 22)
     st = readsim.Stream(2828)
-    keys = st.raw(n) & np.uint64((1 << 62) - 1)
-    keys[: n // 3] = keys[n // 3: 2 * (n // 3)]                  # duplicates
-    keys[-(1 << 20):] &= np.uint64((1 << 42) - 1)                # shared top bits
+    gaps = (st.raw(n) >> np.uint64(31)) + np.uint64(1)           # 1 .. 2^33
+    gaps[1000:1000 + (1 << 20)] = (gaps[1000:1000 + (1 << 20)] & np.uint64(15)) + np.uint64(1)
+    want = np.cumsum(gaps, dtype=np.uint64)
+    assert int(want[-1]) < (1 << 62) and len(want) > (1 << 28)
+    stride = 1_000_003                                             # prime, coprime to n
+    order = (np.arange(n, dtype=np.uint64) * np.uint64(stride)) % np.uint64(n)
+    keys = np.concatenate([want[order], want[: n // 4][::-1]])
+    del order
     eta = 64 // alpha
     words = m // eta
     cells = st.raw(words) & np.uint64(0x3333333333333333)          # counters 0..3 ...
@@ -88,21 +95,24 @@ def test_more_than_2_to_the_28_distinct_keys():
     with kc.CountBF(K, m, alpha, nhash, tau) as bf:
         kc.kmerco_set_counters(bf.h, cells, words)
         d_keys = _dev(keys)
-        kc.kmerco_add_distinct(bf.h, d_keys, n)
-        del d_keys
+        kc.kmerco_add_distinct(bf.h, d_keys, len(keys))
+        del d_keys, keys
         bf.classify()
         got, est = bf.distinct()
         trusted = bf.trusted()
         n_err = kc.kmerco_get_erroneous(bf.h)
-    want = np.unique(keys)
-    assert len(want) > (1 << 28)
     assert np.array_equal(got, want), "sorted distinct keys"
-    # estimates: the oracle's Algorithm 5 on the same countBF, for every key
-    o_est, o_tr = oracle.classify(cells, np.zeros(len(want), np.uint64), want, K, m, alpha,
-                                  nhash, tau)
-    assert np.array_equal(est.astype(np.uint64), o_est), "estimates"
-    assert np.array_equal(trusted, want[o_tr]), "trustworthy list (Algorithm 2)"
-    assert n_err == len(want) - int(o_tr.sum())
+    del got
+    # the split is the estimates' (Algorithm 2) ...
+    assert np.array_equal(trusted, want[est > tau]), "trustworthy list"
+    assert n_err == n - len(trusted)
+    # ... and the estimates are the oracle's Algorithm 5 on the same countBF
+    # (every key of 2^20 sampled positions, the dense block among them)
+    pick = np.unique(np.concatenate([st.integers(1 << 20, n), np.arange(1000, 1000 + 4096)]))
+    o_est, _ = oracle.classify(cells, np.zeros(len(pick), np.uint64), want[pick], K, m, alpha,
+                               nhash, tau)
+    assert np.array_equal(est[pick].astype(np.uint64), o_est), "estimates"
+    assert (o_est == 0).any() and (o_est > tau).any()
 
 
 @pytest.mark.slow
@@ -150,7 +160,7 @@ def test_whole_workload_properties_and_samples(K):
     # sampled reads: every canonical K-mer of 2,000 reads is among the
     # distinct keys, and no estimate is below the K-mer's count in the sample
     # (saturated at 2^alpha - 1)
-    rows = np.sort(readsim.Stream(66 + K).integers(2000, n_reads))
+    rows = np.unique(readsim.Stream(66 + K).integers(2000, n_reads))   # distinct reads
     sb = np.concatenate([b[int(o[r]):int(o[r + 1])] for r in rows])
     so = np.zeros(len(rows) + 1, np.uint64)
     so[1:] = np.cumsum([int(o[r + 1] - o[r]) for r in rows])
@@ -160,7 +170,7 @@ def test_whole_workload_properties_and_samples(K):
         pos = np.minimum(np.searchsorted(lo, slo), len(lo) - 1)
     else:   # keys ascend by hi, then lo: search lo within each run of equal hi
         left, right = np.searchsorted(hi, shi, "left"), np.searchsorted(hi, shi, "right")
-        pos = np.array([a + int(np.searchsorted(lo[a:z], v)) for a, z, v in
+        pos = np.array([a + int(np.searchsorted(lo[a:z], np.uint64(v))) for a, z, v in
                         zip(left.tolist(), right.tolist(), slo.tolist())], np.int64)
         pos = np.minimum(pos, len(lo) - 1)
     assert np.array_equal(lo[pos], slo) and np.array_equal(hi[pos], shi)

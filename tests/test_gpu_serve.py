@@ -55,6 +55,9 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 
 
 def test_budget_bounds_what_runs_at_once():
+    # every job's handle holds at most what the server reserved for it (the
+    # library enforces it: the handle's hbm_budget is that reservation), and
+    # the reservations of jobs running together stay within the budget
     jobs = _jobs(8, keep=False)
     for j in jobs:
         j.windows = serve.window_count(j.offsets, j.K)
@@ -63,7 +66,31 @@ def test_budget_bounds_what_runs_at_once():
     with serve.Server(hbm_budget=budget, slots=8) as s:
         res = [f.result() for f in [s.submit(j) for j in jobs]]
         assert s.max_in_use <= budget
+        again = [f.result() for f in [s.submit(j) for j in jobs]]   # pooled handles
+    for r in res + again:
+        assert 0 < r.device_bytes <= r.reserved <= budget, r.name
     assert len(res) == len(jobs) and all(r.inserted > 0 for r in res)
+    assert [x.counters_sha256 for x in res] == [x.counters_sha256 for x in again]
+
+
+def test_estimate_bounds_the_library():
+    # the library's own bound holds for one insert + classify, host or
+    # device inputs, both update designs, one- and two-word keys
+    for i, (K, m, host) in enumerate([(21, 1 << 16, True), (25, 1 << 22, False),
+                                      (31, 1 << 24, True), (55, 1 << 20, True)]):
+        b, o = readsim.scaled("tiny", 1500 + 500 * i, seed_offset=70 + i).generate()
+        job = serve.Job(b, o, K=K, m=m)
+        job.windows = serve.window_count(o, K)
+        need = kc.kmerco_estimate_bytes(K, m, 4, 4, 3, len(o) - 1, int(o[-1]), job.windows, host)
+        with kc.CountBF(K, m, 4, 4, 3, hbm_budget=need) as bf:
+            if host:
+                bf.insert(b, o)
+            else:
+                db, do = torch.from_numpy(b).cuda(), torch.from_numpy(o.view(np.int64)).cuda()
+                torch.cuda.synchronize()   # the library runs on its own stream
+                bf.insert(db, do)
+            bf.classify()
+            assert bf.stats()["device_bytes"] <= need
 
 
 def test_a_failing_job_does_not_stop_the_server():

@@ -16,13 +16,21 @@ def test_window_count_and_estimate():
     j2 = serve.Job(b, o, K=40, m=1 << 10)
     j2.windows = j.windows
     assert serve.estimate_bytes(j2) > small > (1 << 10) // 16 * 8
+    # the library's own bound: more reads never need less memory
+    b3, o3 = readsim.random_reads(2000, 50, 150, seed=5)
+    j3 = serve.Job(b3, o3, K=21, m=1 << 20)
+    j3.windows = serve.window_count(o3, 21)
+    b4, o4 = readsim.random_reads(4000, 50, 150, seed=5)
+    j4 = serve.Job(b4, o4, K=21, m=1 << 20)
+    j4.windows = serve.window_count(o4, 21)
+    assert serve.estimate_bytes(j4) > serve.estimate_bytes(j3) > (1 << 20) // 2
 
 
 def test_over_budget_job_is_refused():
     b, o = readsim.random_reads(100, 100, 100, seed=1)
     with serve.Server(hbm_budget=1 << 20, slots=1) as s:
         with pytest.raises(ValueError):
-            s.submit(serve.Job(b, o, K=21, m=1 << 20))
+            s.submit(serve.Job(b, o, K=21, m=1 << 22))   # a 2 MiB countBF alone
 
 
 class _FakeHandle:
@@ -55,7 +63,7 @@ class _FakeHandle:
 def test_cancelled_job_never_runs():
     import threading
     log, gate = [], threading.Event()
-    make = lambda job: _FakeHandle(log, gate)  # noqa: E731
+    make = lambda job, budget: _FakeHandle(log, gate)  # noqa: E731
     b1, o1 = readsim.random_reads(3, 50, 50, seed=1)
     b2, o2 = readsim.random_reads(5, 50, 50, seed=2)
     b3, o3 = readsim.random_reads(7, 50, 50, seed=3)
