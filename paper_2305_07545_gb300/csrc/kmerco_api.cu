@@ -84,6 +84,8 @@ struct kmerco {
     unsigned long long *bucket_host;      // pinned copy of the bucket starts
     unsigned short *hist_partial;         // per-block partial histograms
     uint64_t hist_partial_cap;
+    unsigned long long *seg_scratch;      // classify of large key sets: segment bounds, big segments
+    uint64_t seg_scratch_cap;
 };
 
 namespace {
@@ -322,6 +324,15 @@ int ceil_log2(uint64_t x) {
     int l = 0;
     while (l < 64 && (1ull << l) < x) ++l;
     return l;
+}
+
+// Classification sorts a distinct-key set this large by its top bits and
+// then by segments in shared memory (top_segment_sort) rather than by a full
+// radix sort or the bucket sort.
+bool use_top_sort(uint64_t D, int kw, int bits) {
+    if (bits < kTopSortBits + 12) return false;
+    if (kw == 2) return D > (1ull << 21);
+    return D > (uint64_t)kHistBins * (kBucketCap / 4);
 }
 
 // ------------------------------------------------------------ insert plan
@@ -592,6 +603,7 @@ int kmerco_estimate_bytes(const kmerco_config_t *cfg, uint64_t nreads, uint64_t 
         const uint64_t D = windows;
         b += 2 * grown(D * kw, 8) + grown(D, 4) + grown(D * kw, 8) +
              grown(sort_scratch_words(D, kw), 4) + grown(split_scratch_words(D), 8);
+        if (use_top_sort(D, t.kw, 2 * t.K)) b += grown(3 * seg_bounds_entries(D, t.kw) + 1, 8);
         if (kw == 1 && 2 * t.K >= kHistBits + 8 && D > 65536)   // the bucket sort may run
             b += grown(kBucketHostWords + kHistBins, 8) +
                  grown(bucket_hist_blocks(D) * kHistBins, 2);
@@ -720,6 +732,7 @@ void kmerco_destroy(kmerco_t *h) {
         dev_free(h, h->part_ctr, h->part_ctr_alloc * 8);
         dev_free(h, h->bucket_scratch, h->bucket_scratch_cap * 8);
         dev_free(h, h->hist_partial, h->hist_partial_cap * 2);
+        dev_free(h, h->seg_scratch, h->seg_scratch_cap * 8);
         if (h->bucket_host) cudaFreeHost(h->bucket_host);
         if (h->ctr_host) cudaFreeHost(h->ctr_host);
         for (int i = 0; i < 4; ++i)
@@ -853,8 +866,41 @@ int kmerco_classify(kmerco_t *h) {
     const int bits = 2 * h->K;
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
     // (small sets: the radix sort, without the bucket sort's fixed scratch)
-    if (kw == 1 && bits >= kHistBits + 8 && D > 65536 &&
-        D <= (uint64_t)kHistBins * (kBucketCap / 4)) {
+    if (use_top_sort(D, kw, bits)) {
+        // three stable passes on the top bits (dlist -> alt0 -> alt1 -> alt0),
+        // then the segments in shared memory
+        const int s0 = bits - kTopSortBits;
+        KM_CUDA(radix_pass(distinct_in, h->alt0, D, kw, s0, h->sort_scratch, h->stream));
+        KM_CUDA(radix_pass(h->alt0, h->alt1, D, kw, s0 + 8, h->sort_scratch, h->stream));
+        KM_CUDA(radix_pass(h->alt1, h->alt0, D, kw, s0 + 16, h->sort_scratch, h->stream));
+        h->launches += 9;
+        const uint64_t nbe = seg_bounds_entries(D, kw);
+        KM_TRY(ensure(h, &h->seg_scratch, &h->seg_scratch_cap, 3 * nbe + 1));
+        unsigned long long *bnd = h->seg_scratch, *big = bnd + nbe, *nbig = big + 2 * nbe;
+        KM_CUDA(top_segment_sort(h->alt0, D, kw, bits, bnd, big, nbig, h->stream));
+        h->launches += 2;
+        KM_TRY(ensure_bucket_host(h));
+        KM_CUDA(cudaMemcpyAsync(h->bucket_host, nbig, 8, cudaMemcpyDeviceToHost, h->stream));
+        KM_CUDA(cudaStreamSynchronize(h->stream));
+        const uint64_t nb = h->bucket_host[0];
+        if (nb) {   // runs of equal top bits longer than a segment: radix sorts of their own
+            std::vector<unsigned long long> list(2 * nb);
+            KM_CUDA(cudaMemcpy(list.data(), big, 2 * nb * 8, cudaMemcpyDeviceToHost));
+            for (uint64_t q = 0; q < nb; ++q) {
+                uint64_t *range = h->alt0 + list[2 * q] * kw;
+                const uint64_t n_b = list[2 * q + 1];
+                const uint64_t *res = range;
+                KM_CUDA(radix_sort(range, h->alt1 + list[2 * q] * kw, range, n_b, kw, bits,
+                                   h->sort_scratch, &res, h->stream));
+                h->launches += 3 * (uint64_t)passes;
+                if (res != range)
+                    KM_CUDA(cudaMemcpyAsync(range, res, n_b * kw * 8, cudaMemcpyDeviceToDevice,
+                                            h->stream));
+            }
+        }
+        sorted = h->alt0;
+    } else if (kw == 1 && bits >= kHistBits + 8 && D > 65536 &&
+               D <= (uint64_t)kHistBins * (kBucketCap / 4)) {
         // Bucket sort: histogram of the top kHistBits key bits, adjacent bins
         // merged into super-buckets of at most kBucketCap keys, each sorted in
         // shared memory.  A single bin above kBucketCap is radix sorted.

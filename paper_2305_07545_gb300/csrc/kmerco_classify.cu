@@ -80,10 +80,28 @@ __device__ __forceinline__ T block_exclusive_scan_n(T v, T &total) {
     return before + x - v;
 }
 
+// The 8-bit digit at bit `shift` of a key (a digit may straddle the two
+// words of a two-word key).
 template <int KW>
 __device__ __forceinline__ unsigned digit_of(const uint64_t *k, int shift) {
-    if (KW == 1 || shift < 64) return (unsigned)(k[0] >> shift) & (kRadixBins - 1);
-    return (unsigned)(k[1] >> (shift - 64)) & (kRadixBins - 1);
+    if (KW == 1 || shift + kRadixBits <= 64) return (unsigned)(k[0] >> shift) & (kRadixBins - 1);
+    if (shift >= 64) return (unsigned)(k[1] >> (shift - 64)) & (kRadixBins - 1);
+    return (unsigned)((k[0] >> shift) | (k[1] << (64 - shift))) & (kRadixBins - 1);
+}
+
+// Bits [s, s + 64) of a key of KW words, as one word (0 <= s < 64 * KW).
+template <int KW>
+__device__ __forceinline__ uint64_t bits_from(const uint64_t *k, int s) {
+    if (KW == 1 || s == 0) return k[0] >> s;
+    if (s >= 64) return k[1] >> (s - 64);
+    return (k[0] >> s) | (k[1] << (64 - s));
+}
+
+// a < b for keys of KW words (two-word keys compare high word first).
+template <int KW>
+__device__ __forceinline__ bool key_less(const uint64_t *a, const uint64_t *b) {
+    if (KW == 1) return a[0] < b[0];
+    return a[1] < b[1] || (a[1] == b[1] && a[0] < b[0]);
 }
 
 template <int KW>
@@ -634,6 +652,181 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort_kernel(
     for (unsigned i = tid; i < n; i += kBucketThreads) data[s0 + i] = B[i];
 }
 
+// ------------------------------------------------------ top-bits + segments
+// Sort of a large key set in two steps.  Three stable radix passes on the
+// top kTopBits key bits order the keys by those bits; the array is then cut
+// into segments that begin where the top bits change, near every multiple
+// of half a segment's capacity, and each segment is sorted in shared memory
+// (a counting sort on 12 more bits, then an insertion or bitonic sort with
+// the whole key as the comparison).  A segment too large for shared memory
+// (one run of equal top bits longer than that) is listed for a radix sort of
+// its own.
+constexpr int kTopBits = kTopSortBits;
+
+template <int KW>
+__host__ __device__ constexpr int seg_cap() { return KW == 1 ? kBucketCap : kBucketCap / 2; }
+
+// Top kTopBits bits of a key of `bits` bits.
+template <int KW>
+__device__ __forceinline__ uint32_t top_bits(const uint64_t *k, int bits) {
+    return (uint32_t)(bits_from<KW>(k, bits - kTopBits) & ((1u << kTopBits) - 1));
+}
+
+// b[j], j < nb: the first index at or after j * H where the top bits differ
+// from those of key j * H - 1 (b[0] = 0, and n once past the end), by a
+// binary search over the keys sorted by their top bits.
+template <int KW>
+__global__ void seg_bounds_kernel(const uint64_t *keys, uint64_t n, int bits, uint64_t H,
+                                  uint64_t nb, unsigned long long *b) {
+    const uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (j >= nb) return;
+    const uint64_t at = j * H;
+    if (j == 0 || at >= n) {
+        b[j] = j == 0 ? 0 : n;
+        return;
+    }
+    const uint32_t t = top_bits<KW>(keys + (at - 1) * KW, bits);
+    uint64_t lo = at, hi = n;   // the answer is in [lo, hi]
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (top_bits<KW>(keys + mid * KW, bits) > t)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    b[j] = lo;
+}
+
+// Segment j = [b[j], b[j + 1]) of `data` sorted in place by one block.
+// Segments above seg_cap<KW>() keys go to the `big` list (begin, count)
+// instead; nbig counts them.
+template <int KW>
+__global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
+    uint64_t *data, int bits, const unsigned long long *b, unsigned long long *big,
+    unsigned long long *nbig) {
+    constexpr int C = seg_cap<KW>();
+    constexpr unsigned kPer = C / kBucketThreads;
+    extern __shared__ unsigned long long sm[];
+    uint64_t *B = (uint64_t *)sm;            // C keys of KW words
+    unsigned *hist = (unsigned *)(sm + C * KW);
+    unsigned *st = hist + kSubBins, *fill = st + kSubBins;
+    __shared__ unsigned maxsub;
+    const uint64_t s0 = b[blockIdx.x], e0 = b[blockIdx.x + 1];
+    if (e0 <= s0 + 1) return;   // empty or one key
+    const uint64_t nn = e0 - s0;
+    if (nn > (uint64_t)C) {
+        if (threadIdx.x == 0) {
+            const unsigned long long q = atomicAdd(nbig, 1ull);
+            big[2 * q] = s0;
+            big[2 * q + 1] = nn;
+        }
+        return;
+    }
+    const unsigned n = (unsigned)nn;
+    const unsigned tid = threadIdx.x;
+    // the segment's top-bit range [t0, t1] maps onto kSubBins sub-bins of
+    // the key's top min(bits, 64) bits
+    const int pb = bits < 64 ? bits : 64;
+    const uint32_t t0 = top_bits<KW>(data + s0 * KW, bits);
+    const uint32_t t1 = top_bits<KW>(data + (e0 - 1) * KW, bits);
+    const int below = pb - kTopBits;                      // prefix bits under the top bits
+    int span = 0;
+    while ((1ull << span) < (uint64_t)(t1 - t0 + 1)) ++span;
+    int r = span + below - 12;
+    if (r < 0) r = 0;
+    const uint64_t base = (uint64_t)t0 << below;
+    for (unsigned i = tid; i < kSubBins; i += kBucketThreads) hist[i] = 0;
+    if (tid == 0) maxsub = 0;
+    __syncthreads();
+    // sub-bin of a key (recomputed where needed: registers hold the keys)
+    auto sub_of = [&](const uint64_t *k) {
+        return (unsigned)min((bits_from<KW>(k, bits - pb) - base) >> r, (uint64_t)kSubBins - 1);
+    };
+    uint64_t key[kPer][KW];
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q) {
+        const unsigned i = q * kBucketThreads + tid;
+#pragma unroll
+        for (int w = 0; w < KW; ++w) key[q][w] = i < n ? data[(s0 + i) * KW + w] : 0ull;
+        if (i < n) atomicAdd(&hist[sub_of(key[q])], 1u);
+    }
+    __syncthreads();
+    {
+        unsigned v[4], sum = 0, mx = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = hist[tid * 4 + j];
+            sum += v[j];
+            mx = max(mx, v[j]);
+        }
+        unsigned tot;
+        unsigned pre = block_exclusive_scan_n<unsigned, kBucketThreads>(sum, tot);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            st[tid * 4 + j] = pre;
+            fill[tid * 4 + j] = pre;
+            pre += v[j];
+        }
+        atomicMax(&maxsub, mx);
+    }
+    __syncthreads();
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q) {
+        if (q * kBucketThreads + tid < n) {
+            const unsigned at = atomicAdd(&fill[sub_of(key[q])], 1u);
+#pragma unroll
+            for (int w = 0; w < KW; ++w) B[at * KW + w] = key[q][w];
+        }
+    }
+    __syncthreads();
+    if (maxsub <= (unsigned)kSubMax) {
+        for (unsigned bin = tid; bin < kSubBins; bin += kBucketThreads) {
+            const unsigned a0 = st[bin], m = hist[bin];
+            for (unsigned i = 1; i < m; ++i) {
+                uint64_t k[KW];
+#pragma unroll
+                for (int w = 0; w < KW; ++w) k[w] = B[(a0 + i) * KW + w];
+                unsigned j = i;
+                while (j > 0 && key_less<KW>(k, B + (a0 + j - 1) * KW)) {
+#pragma unroll
+                    for (int w = 0; w < KW; ++w) B[(a0 + j) * KW + w] = B[(a0 + j - 1) * KW + w];
+                    --j;
+                }
+#pragma unroll
+                for (int w = 0; w < KW; ++w) B[(a0 + j) * KW + w] = k[w];
+            }
+        }
+    } else {   // clustered keys: bitonic sort of the whole segment (all-ones pads sort last)
+        unsigned P = 2;
+        while (P < n) P <<= 1;
+        for (unsigned i = n + tid; i < P; i += kBucketThreads)
+#pragma unroll
+            for (int w = 0; w < KW; ++w) B[i * KW + w] = ~0ull;
+        __syncthreads();
+        for (unsigned k = 2; k <= P; k <<= 1) {
+            for (unsigned j = k >> 1; j > 0; j >>= 1) {
+                for (unsigned i = tid; i < P; i += kBucketThreads) {
+                    const unsigned ixj = i ^ j;
+                    if (ixj > i) {
+                        const bool up = (i & k) == 0;
+                        if (key_less<KW>(B + ixj * KW, B + i * KW) == up) {
+#pragma unroll
+                            for (int w = 0; w < KW; ++w) {
+                                const uint64_t t = B[i * KW + w];
+                                B[i * KW + w] = B[ixj * KW + w];
+                                B[ixj * KW + w] = t;
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    __syncthreads();
+    for (unsigned i = tid; i < n * KW; i += kBucketThreads) data[s0 * KW + i] = B[i];
+}
+
 uint32_t sort_tiles(uint64_t n, int kw) {
     const uint64_t t = kw == 1 ? (uint64_t)tile_keys<1>() : (uint64_t)tile_keys<2>();
     return (uint32_t)((n + t - 1) / t);
@@ -692,6 +885,59 @@ cudaError_t bucket_place_and_sort(const uint64_t *in, uint64_t *out, uint64_t n,
 
 uint64_t sort_scratch_words(uint64_t n, int kw) {
     return (uint64_t)kRadixBins * sort_tiles(n, kw) + kRadixBins;
+}
+
+cudaError_t radix_pass(const uint64_t *src, uint64_t *dst, uint64_t n, int kw, int shift,
+                       uint32_t *counts, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint32_t ntiles = sort_tiles(n, kw);
+    uint32_t *totals = counts + (uint64_t)kRadixBins * ntiles;
+    if (kw == 1) {
+        upsweep_kernel<1><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
+        scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
+        downsweep_kernel<1><<<ntiles, down_threads<1>(), 0, s>>>(src, dst, n, shift, counts, totals,
+                                                            ntiles);
+    } else {
+        upsweep_kernel<2><<<ntiles, kSortThreads, 0, s>>>(src, n, shift, counts, ntiles);
+        scan_rows_kernel<<<kRadixBins, kSortThreads, 0, s>>>(counts, ntiles, totals);
+        downsweep_kernel<2><<<ntiles, down_threads<2>(), 0, s>>>(src, dst, n, shift, counts, totals,
+                                                            ntiles);
+    }
+    return cudaGetLastError();
+}
+
+uint64_t seg_half(int kw) { return (uint64_t)(kw == 1 ? seg_cap<1>() : seg_cap<2>()) / 2; }
+
+uint64_t seg_bounds_entries(uint64_t n, int kw) { return (n + seg_half(kw) - 1) / seg_half(kw) + 2; }
+
+cudaError_t top_segment_sort(uint64_t *data, uint64_t n, int kw, int bits, unsigned long long *b,
+                             unsigned long long *big, unsigned long long *nbig, cudaStream_t s) {
+    if (bits < kTopBits + 12) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    const uint64_t H = seg_half(kw);
+    const uint64_t nb = (n + H - 1) / H + 1;   // b[0..nb-1], the last one n
+    const unsigned g = (unsigned)((nb + 255) / 256);
+    if (kw == 1)
+        seg_bounds_kernel<1><<<g, 256, 0, s>>>(data, n, bits, H, nb, b);
+    else
+        seg_bounds_kernel<2><<<g, 256, 0, s>>>(data, n, bits, H, nb, b);
+    const int smem1 = seg_cap<1>() * 8 + 3 * kSubBins * 4;
+    const int smem2 = seg_cap<2>() * 16 + 3 * kSubBins * 4;
+    if (kw == 1) {
+        e = cudaFuncSetAttribute(segment_sort_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem1);
+        if (e != cudaSuccess) return e;
+        segment_sort_kernel<1><<<(unsigned)(nb - 1), kBucketThreads, smem1, s>>>(data, bits, b, big,
+                                                                               nbig);
+    } else {
+        e = cudaFuncSetAttribute(segment_sort_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem2);
+        if (e != cudaSuccess) return e;
+        segment_sort_kernel<2><<<(unsigned)(nb - 1), kBucketThreads, smem2, s>>>(data, bits, b, big,
+                                                                               nbig);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint64_t n, int kw,

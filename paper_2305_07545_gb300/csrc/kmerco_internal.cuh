@@ -334,6 +334,21 @@ cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *
 uint64_t sort_scratch_words(uint64_t n, int kw);
 cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint64_t n, int kw,
                        int bits, uint32_t *counts, const uint64_t **result, cudaStream_t s);
+// One stable pass of radix_sort on the 8-bit digit at bit `shift`.
+cudaError_t radix_pass(const uint64_t *src, uint64_t *dst, uint64_t n, int kw, int shift,
+                       uint32_t *counts, cudaStream_t s);
+
+// Large key sets: after three radix_pass calls on the top kTopSortBits of
+// the 2K key bits, top_segment_sort finishes the sort in place: the keys are
+// cut into segments where their top bits change (b: seg_bounds_entries(n, kw)
+// words) and each segment is sorted in shared memory.  Segments too large
+// for it are written to big as (begin, count) pairs, their number to *nbig
+// (at most seg_bounds_entries words of pairs); the caller radix-sorts them.
+// Needs 2K >= kTopSortBits + 12.
+constexpr int kTopSortBits = 24;
+uint64_t seg_bounds_entries(uint64_t n, int kw);
+cudaError_t top_segment_sort(uint64_t *data, uint64_t n, int kw, int bits, unsigned long long *b,
+                             unsigned long long *big, unsigned long long *nbig, cudaStream_t s);
 
 
 // Bucket sort of one-word keys (classify): bucket_histogram counts

@@ -441,6 +441,26 @@ def test_segmented_sort_of_large_key_sets(K, prefix):
     check(g, b, o, K, 4, 3, 2)
 
 
+@pytest.mark.parametrize("K,prefix", [(33, 0), (55, 0), (64, 0), (40, 30)])
+def test_top_bits_sort_of_large_two_word_key_sets(K, prefix):
+    # over 2^21 distinct two-word keys take the top-bits sort: three radix
+    # passes on the top 24 key bits (for K = 33 one digit straddles the two
+    # key words), then segments sorted in shared memory; with a long shared
+    # prefix one run of equal top bits outgrows a segment and is radix sorted
+    # on its own
+    rng = readsim.Stream(1900 + K + prefix)
+    n_reads, length = 40000, 130
+    codes = np.frombuffer(b"ACGT", np.uint8)[rng.integers(n_reads * length, 4)]
+    reads = codes.reshape(n_reads, length)
+    if prefix:
+        reads[: n_reads // 2, :prefix] = ord("A")
+    b = np.ascontiguousarray(reads).reshape(-1)
+    o = np.arange(0, n_reads * length + 1, length, dtype=np.uint64)
+    g = gpu_run(b, o, K, 1 << 24, 4, 3, 2)
+    assert g["stats"]["distinct"] > (1 << 21)
+    check(g, b, o, K, 4, 3, 2, cross_check=False)
+
+
 @pytest.mark.parametrize("update_mode", [kc.UPDATE_ATOMIC, kc.UPDATE_PARTITIONED])
 def test_host_inputs_in_pieces_and_back_to_back_calls(update_mode):
     # two host-input calls in a row reuse the staging buffer: the second
