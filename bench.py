@@ -344,6 +344,9 @@ def time_workload(name: str, args, bases, offsets, d_bases, d_offsets, flush, cl
     import paper_2305_07545_gb300 as kc
 
     w = readsim.WORKLOADS[name]
+    if args.counters:
+        import dataclasses
+        w = dataclasses.replace(w, m=args.counters)
     dev = torch.cuda.current_device()
     nreads = len(offsets) - 1
     lens = np.diff(offsets.astype(np.int64))
@@ -488,7 +491,7 @@ def run_ours(args) -> None:
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     torch.cuda.synchronize()
 
-    full_size = not args.reads
+    full_size = not args.reads and not args.counters
     input_bytes = bases.nbytes + offsets.nbytes
     peak, peak_src = measured_peak()
     r = time_workload(name, args, bases, offsets, d_bases, d_offsets, flush, clock_dev, world,
@@ -529,7 +532,8 @@ def run_ours(args) -> None:
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic",
-            "config": {"workload": describe(wl), "K": w.K, "m": w.m, "counter_bits": w.alpha,
+            "config": {"workload": describe(wl), "K": w.K, "m": r["workload"].m,
+                       "counter_bits": w.alpha,
                        "nhash": w.nhash, "tau": w.tau, "reads_per_gpu": len(offsets) - 1,
                        "kmers_per_step_per_gpu": r["inserted"], "distinct_per_gpu": r["distinct"],
                        "trustworthy_per_gpu": r["trusted"],
@@ -737,6 +741,8 @@ def main(argv=None) -> None:
                     help="reads per step of the reference (oracle) arm (default: per workload)")
     ap.add_argument("--reads", type=int, default=0,
                     help="reads per GPU (default: the workload's own count; smaller for profiling)")
+    ap.add_argument("--counters", type=int, default=0,
+                    help="countBF counters (default: the workload's own; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",

@@ -302,7 +302,9 @@ int kmerco_merge(kmerco_t *dst, kmerco_t *src);
  *  - every call shares that array, so calls that overlap on the GPU (other
  *    streams, other host threads) race and must be serialised by the caller;
  *  - the first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress; make that first call before any stream capture.
+ *    cudaGetSymbolAddress, and so does the first call in a new CUDA context
+ *    of the device (after cudaDeviceReset); make that first call before
+ *    any stream capture.
  * Runs on `stream` (a cudaStream_t; NULL is the legacy default stream) and
  * synchronises it before returning.  Errors: EINVAL (argument out of range,
  * NULL pointer, n too large), ECUDA.

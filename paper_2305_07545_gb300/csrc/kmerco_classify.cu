@@ -22,64 +22,6 @@ namespace {
 
 constexpr int kWarps = kSortThreads / 32;
 
-// Exclusive scan across a 256-thread block; `total` receives the block sum.
-template <typename T>
-__device__ __forceinline__ T block_exclusive_scan(T v, T &total) {
-    __shared__ T warp_sums[kWarps];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        T s = lane < kWarps ? warp_sums[lane] : T(0);
-#pragma unroll
-        for (int o = 1; o < kWarps; o <<= 1) {
-            T y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        if (lane < kWarps) warp_sums[lane] = s;
-    }
-    __syncthreads();
-    T before = warp ? warp_sums[warp - 1] : T(0);
-    total = warp_sums[kWarps - 1];
-    __syncthreads();
-    return before + x - v;
-}
-
-// Exclusive scan across a block of NT threads.
-template <typename T, int NT>
-__device__ __forceinline__ T block_exclusive_scan_n(T v, T &total) {
-    __shared__ T wsum[NT / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        T s = lane < NT / 32 ? wsum[lane] : T(0);
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        if (lane < NT / 32) wsum[lane] = s;
-    }
-    __syncthreads();
-    T before = warp ? wsum[warp - 1] : T(0);
-    total = wsum[NT / 32 - 1];
-    __syncthreads();
-    return before + x - v;
-}
-
 // The 8-bit digit at bit `shift` of a key (a digit may straddle the two
 // words of a two-word key).
 template <int KW>
@@ -140,7 +82,7 @@ __global__ void __launch_bounds__(kSortThreads) scan_rows_kernel(uint32_t *count
             sum += v[j];
         }
         uint32_t tot;
-        uint32_t pre = block_exclusive_scan<uint32_t>(sum, tot) + carry;
+        uint32_t pre = block_exclusive_scan<uint32_t, kSortThreads>(sum, tot) + carry;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             uint32_t idx = s0 + threadIdx.x * 4 + j;
@@ -229,9 +171,9 @@ __global__ void __launch_bounds__(down_threads<KW>(), KW == 1 ? 2 : 3) downsweep
             t64 = totals[d];
         }
         uint32_t tot;
-        const uint32_t ts = block_exclusive_scan_n<uint32_t, NT>(run, tot);
+        const uint32_t ts = block_exclusive_scan<uint32_t, NT>(run, tot);
         uint64_t dtot;
-        const uint64_t dbase = block_exclusive_scan_n<uint64_t, NT>(t64, dtot);
+        const uint64_t dbase = block_exclusive_scan<uint64_t, NT>(t64, dtot);
         if (d < kRadixBins) {
             tstart[d] = ts;
             gofs[d] = dbase + counts[(uint64_t)d * ntiles + blockIdx.x];
@@ -317,7 +259,7 @@ __global__ void __launch_bounds__(kSortThreads) split_count_kernel(const uint32_
         c += (i < n) && est[i] > tau;
     }
     unsigned long long tot;
-    block_exclusive_scan<unsigned long long>(c, tot);
+    block_exclusive_scan<unsigned long long, kSortThreads>(c, tot);
     if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
 }
 
@@ -328,7 +270,7 @@ __global__ void __launch_bounds__(kSortThreads) split_scan_kernel(uint64_t *tile
     for (uint64_t s0 = 0; s0 < ntiles; s0 += kSortThreads) {
         const uint64_t idx = s0 + threadIdx.x;
         unsigned long long v = idx < ntiles ? tile_cnt[idx] : 0ull, tot;
-        unsigned long long pre = block_exclusive_scan<unsigned long long>(v, tot) + carry;
+        unsigned long long pre = block_exclusive_scan<unsigned long long, kSortThreads>(v, tot) + carry;
         if (idx < ntiles) tile_cnt[idx] = pre;
         carry += tot;
     }
@@ -535,7 +477,7 @@ __global__ void __launch_bounds__(1024) bucket_scatter_sorted_kernel(
         unsigned sum = 0;
         for (unsigned j = 0; j < per && b0 + j < nsuper; ++j) sum += h[b0 + j];
         unsigned tot;
-        unsigned pre = block_exclusive_scan_n<unsigned, kT>(sum, tot);
+        unsigned pre = block_exclusive_scan<unsigned, kT>(sum, tot);
         for (unsigned j = 0; j < per && b0 + j < nsuper; ++j) {
             const unsigned b = b0 + j, m = h[b];
             lst[b] = pre;
@@ -596,7 +538,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort_kernel(
             mx = max(mx, v[j]);
         }
         unsigned tot;
-        unsigned pre = block_exclusive_scan_n<unsigned, kBucketThreads>(sum, tot);
+        unsigned pre = block_exclusive_scan<unsigned, kBucketThreads>(sum, tot);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             st[tid * 4 + j] = pre;
@@ -760,7 +702,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
             mx = max(mx, v[j]);
         }
         unsigned tot;
-        unsigned pre = block_exclusive_scan_n<unsigned, kBucketThreads>(sum, tot);
+        unsigned pre = block_exclusive_scan<unsigned, kBucketThreads>(sum, tot);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             st[tid * 4 + j] = pre;

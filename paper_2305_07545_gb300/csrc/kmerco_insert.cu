@@ -744,32 +744,13 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
 }
 
 // Exclusive prefix sum of v[0..n) into out[0..n), n <= 2 * kRepartThreads,
-// by the whole block (two entries per thread, warp shuffles, warp totals).
+// by the whole block (two entries per thread).
 __device__ __forceinline__ void repart_scan(const unsigned *v, unsigned *out, unsigned n) {
-    __shared__ unsigned warp_sum[kRepartThreads / 32];
-    const unsigned tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned tid = threadIdx.x;
     const unsigned v0 = 2 * tid < n ? v[2 * tid] : 0u;
     const unsigned v1 = 2 * tid + 1 < n ? v[2 * tid + 1] : 0u;
-    unsigned incl = v0 + v1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (unsigned)o) incl += t;
-    }
-    if (lane == 31) warp_sum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned x = lane < kRepartThreads / 32 ? warp_sum[lane] : 0u;
-        unsigned wi = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned t = __shfl_up_sync(0xffffffffu, wi, o);
-            if (lane >= (unsigned)o) wi += t;
-        }
-        if (lane < kRepartThreads / 32) warp_sum[lane] = wi - x;
-    }
-    __syncthreads();
-    const unsigned off = warp_sum[warp] + incl - (v0 + v1);
+    unsigned tot;
+    const unsigned off = block_exclusive_scan<unsigned, kRepartThreads>(v0 + v1, tot);
     if (2 * tid < n) out[2 * tid] = off;
     if (2 * tid + 1 < n) out[2 * tid + 1] = off + v0;
 }

@@ -211,6 +211,40 @@ __device__ __forceinline__ void address(const Geometry &G, uint64_t h, uint64_t 
     }
 }
 
+// ------------------------------------------------------------ block scan
+// Exclusive prefix sum of one value per thread across a block of NT threads
+// (a multiple of 32, at most 1024): warp shuffles, then a scan of the warp
+// totals by the first warp.  `total` receives the block's sum.  Every thread
+// of the block must call it; it synchronises the block.
+template <typename T, int NT>
+__device__ __forceinline__ T block_exclusive_scan(T v, T &total) {
+    static_assert(NT % 32 == 0 && NT <= 1024, "whole warps, one block");
+    __shared__ T wsum[NT / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < NT / 32 ? wsum[lane] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    const T before = warp ? wsum[warp - 1] : T(0);
+    total = wsum[NT / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
 // ---------------------------------------------------------------- K-mers
 // Reverse complement of a packed K-mer (K <= 32; the key fills the low 2K
 // bits, first base most significant): complement every 2-bit code (3 - c == ~c), reverse the order of the

@@ -30,33 +30,6 @@ static_assert(kMaxTiles * kTile == KMERCO_NOALLOC_MAX_KEYS, "whole tiles");
 // reading them, so nothing has to start at zero.
 static __device__ __align__(256) unsigned long long g_split_scratch[kMaxTiles + 1];
 
-template <typename T>
-__device__ __forceinline__ T scan_block(T v, T &total) {
-    __shared__ T sums[kThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        T y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        T s = lane < kThreads / 32 ? sums[lane] : T(0);
-#pragma unroll
-        for (int o = 1; o < kThreads / 32; o <<= 1) {
-            T y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        if (lane < kThreads / 32) sums[lane] = s;
-    }
-    __syncthreads();
-    T before = warp ? sums[warp - 1] : T(0);
-    total = sums[kThreads / 32 - 1];
-    __syncthreads();
-    return before + x - v;
-}
 
 __global__ void __launch_bounds__(kThreads) count_kernel(const uint32_t *est, uint64_t n,
                                                          uint32_t tau, unsigned long long *scratch) {
@@ -65,7 +38,7 @@ __global__ void __launch_bounds__(kThreads) count_kernel(const uint32_t *est, ui
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) c += (base + j < n) && est[base + j] > tau;
     unsigned long long tot;
-    scan_block<unsigned long long>(c, tot);
+    block_exclusive_scan<unsigned long long, kThreads>(c, tot);
     if (threadIdx.x == 0) scratch[blockIdx.x] = tot;
 }
 
@@ -75,7 +48,7 @@ __global__ void __launch_bounds__(kThreads) scan_kernel(unsigned long long *scra
     for (uint64_t s0 = 0; s0 < ntiles; s0 += kThreads) {
         const uint64_t i = s0 + threadIdx.x;
         unsigned long long v = i < ntiles ? scratch[i] : 0ull, tot;
-        const unsigned long long pre = scan_block<unsigned long long>(v, tot) + carry;
+        const unsigned long long pre = block_exclusive_scan<unsigned long long, kThreads>(v, tot) + carry;
         if (i < ntiles) scratch[i] = pre;
         carry += tot;
     }
@@ -98,7 +71,7 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *keys,
         c += t;
     }
     unsigned long long tot;
-    const unsigned long long pre = scan_block<unsigned long long>(c, tot);
+    const unsigned long long pre = block_exclusive_scan<unsigned long long, kThreads>(c, tot);
     const uint64_t T = scratch[kMaxTiles];
     const uint64_t tile_trusted = scratch[blockIdx.x];
     uint64_t tpos = tile_trusted + pre;
@@ -112,12 +85,50 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const uint64_t *keys,
     }
 }
 
-// Device address of g_split_scratch on the current device, looked up once per
-// device.  In host code the array's name only stands for the device object;
-// the runtime has to translate it.
+// Device address of g_split_scratch on the current device.  In host code
+// the array's name only stands for the device object; the runtime has to
+// translate it, which is done once per device and CUDA context: the address
+// is cached with the identity of the context it was taken in, so that after
+// cudaDeviceReset (a new context on the same device) it is looked up again
+// instead of reusing an address of the destroyed context.
 std::mutex g_mutex;
 constexpr int kMaxDevices = 64;
-unsigned long long *g_scratch_ptr[kMaxDevices];
+struct ScratchAddr {
+    unsigned long long *ptr;
+    unsigned long long ctx;   // cuCtxGetId of the context it was taken in; 0 unknown
+};
+ScratchAddr g_scratch[kMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void **ctx);                       // cuCtxGetCurrent
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);     // cuCtxGetId
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// Unique id of the calling thread's current CUDA context, 0 when there is
+// none or the driver does not tell (the caller then looks the address up
+// again).  The driver functions are reached through the runtime's entry
+// point query, so the library needs no link to the driver library.
+unsigned long long current_context_id() {
+    if (!g_ctx_fns_tried) {
+        g_ctx_fns_tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_current = (CtxGetCurrentFn)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            g_ctx_id = (CtxGetIdFn)f;
+        cudaGetLastError();
+    }
+    if (!g_ctx_current || !g_ctx_id) return 0;
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != 0 || !ctx || g_ctx_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 int scratch_on_current_device(unsigned long long **out) {
     int dev = -1;
@@ -126,15 +137,18 @@ int scratch_on_current_device(unsigned long long **out) {
         return KMERCO_ECUDA;
     }
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    ScratchAddr &a = g_scratch[dev];
+    if (!a.ptr || ctx == 0 || a.ctx != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_split_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return KMERCO_ECUDA;
         }
-        g_scratch_ptr[dev] = (unsigned long long *)p;
+        a.ptr = (unsigned long long *)p;
+        a.ctx = current_context_id();   // the lookup made the device's context current
     }
-    *out = g_scratch_ptr[dev];
+    *out = a.ptr;
     return KMERCO_OK;
 }
 

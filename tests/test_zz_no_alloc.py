@@ -13,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 import readsim
 
 torch = pytest.importorskip("torch")
@@ -50,6 +51,12 @@ def test_noalloc_matches_handle_classify(K):
     stream = torch.cuda.current_stream().cuda_stream
     torch.cuda.synchronize()
 
+    # what the oracle's Algorithm 5 / Algorithm 2 give on the same countBF
+    host_cells = cells.cpu().numpy().view(np.uint64)
+    hi = keys[:, 1].copy() if kw == 2 else np.zeros(n, np.uint64)
+    lo = keys[:, 0].copy() if kw == 2 else keys
+    o_est, o_tr = oracle.classify(host_cells, hi, lo, K, m, alpha, nhash, tau)
+
     # two calls in a row on the same inputs
     for _ in range(2):
         est.zero_()
@@ -61,6 +68,9 @@ def test_noalloc_matches_handle_classify(K):
         got = out.cpu().numpy().view(np.uint64).reshape(keys.shape)
         assert np.array_equal(got[:nt], trusted_ref)
         assert np.array_equal(got[nt:], erroneous_ref)
+        assert np.array_equal(est.cpu().numpy().view(np.uint32).astype(np.uint64), o_est)
+        assert nt == int(o_tr.sum())
+        assert np.array_equal(got[:nt], keys[o_tr]) and np.array_equal(got[nt:], keys[~o_tr])
 
     # a smaller call right after: the scratch left by the larger one is stale
     half = n // 2 + 77
