@@ -878,15 +878,18 @@ int kmerco_classify(kmerco_t *h) {
         KM_TRY(ensure(h, &h->seg_scratch, &h->seg_scratch_cap, 3 * nbe + 1));
         unsigned long long *bnd = h->seg_scratch, *big = bnd + nbe, *nbig = big + 2 * nbe;
         KM_CUDA(top_segment_sort(h->alt0, D, kw, bits, bnd, big, nbig, h->stream));
-        h->launches += 2;
+        // runs of equal top bits longer than a segment: one block each ...
+        KM_CUDA(big_segment_sort(h->alt0, h->alt1, D, kw, bits, big, nbig, h->stream));
+        h->launches += 3;
         KM_TRY(ensure_bucket_host(h));
         KM_CUDA(cudaMemcpyAsync(h->bucket_host, nbig, 8, cudaMemcpyDeviceToHost, h->stream));
         KM_CUDA(cudaStreamSynchronize(h->stream));
         const uint64_t nb = h->bucket_host[0];
-        if (nb) {   // runs of equal top bits longer than a segment: radix sorts of their own
+        if (nb) {   // ... and the few too long for one block: radix sorts of their own
             std::vector<unsigned long long> list(2 * nb);
             KM_CUDA(cudaMemcpy(list.data(), big, 2 * nb * 8, cudaMemcpyDeviceToHost));
             for (uint64_t q = 0; q < nb; ++q) {
+                if (list[2 * q + 1] <= big_segment_max()) continue;
                 uint64_t *range = h->alt0 + list[2 * q] * kw;
                 const uint64_t n_b = list[2 * q + 1];
                 const uint64_t *res = range;

@@ -604,6 +604,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort_kernel(
 // (one run of equal top bits longer than that) is listed for a radix sort of
 // its own.
 constexpr int kTopBits = kTopSortBits;
+constexpr unsigned kRankMax = 256;   // largest sub-bin rank-sorted in a segment
 
 template <int KW>
 __host__ __device__ constexpr int seg_cap() { return KW == 1 ? kBucketCap : kBucketCap / 2; }
@@ -721,23 +722,23 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
         }
     }
     __syncthreads();
-    if (maxsub <= (unsigned)kSubMax) {
-        for (unsigned bin = tid; bin < kSubBins; bin += kBucketThreads) {
+    if (maxsub <= (unsigned)kRankMax) {
+        // rank sort inside each sub-bin: a key's place is the number of keys
+        // of its sub-bin below it (the keys are distinct); neighbouring
+        // threads mostly share a sub-bin, so the loop reads are broadcasts.
+        // Each key goes straight to its place in global memory.
+        for (unsigned i = tid; i < n; i += kBucketThreads) {
+            uint64_t k[KW];
+#pragma unroll
+            for (int w = 0; w < KW; ++w) k[w] = B[i * KW + w];
+            const unsigned bin = sub_of(k);
             const unsigned a0 = st[bin], m = hist[bin];
-            for (unsigned i = 1; i < m; ++i) {
-                uint64_t k[KW];
+            unsigned r = 0;
+            for (unsigned j = a0; j < a0 + m; ++j) r += key_less<KW>(B + j * KW, k) ? 1u : 0u;
 #pragma unroll
-                for (int w = 0; w < KW; ++w) k[w] = B[(a0 + i) * KW + w];
-                unsigned j = i;
-                while (j > 0 && key_less<KW>(k, B + (a0 + j - 1) * KW)) {
-#pragma unroll
-                    for (int w = 0; w < KW; ++w) B[(a0 + j) * KW + w] = B[(a0 + j - 1) * KW + w];
-                    --j;
-                }
-#pragma unroll
-                for (int w = 0; w < KW; ++w) B[(a0 + j) * KW + w] = k[w];
-            }
+            for (int w = 0; w < KW; ++w) data[(s0 + a0 + r) * KW + w] = k[w];
         }
+        return;
     } else {   // clustered keys: bitonic sort of the whole segment (all-ones pads sort last)
         unsigned P = 2;
         while (P < n) P <<= 1;
@@ -767,6 +768,113 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
     }
     __syncthreads();
     for (unsigned i = tid; i < n * KW; i += kBucketThreads) data[s0 * KW + i] = B[i];
+}
+
+// Segments above seg_cap<KW>() keys (runs of equal top bits), one block each:
+// a stable LSD radix sort of the segment in global memory, ping-ponging with
+// the same range of `alt`.  When the whole segment shares its top bits only
+// the bits below them are sorted.  Per pass: the segment's digit histogram
+// and its scan, then its tiles of kBigTile keys in order, each key ranked
+// stably among the equal digits of its warp (one ballot per digit bit) and
+// of the warps before it, and stored behind the keys of earlier tiles with
+// the same digit.  Segments above kBigSegMax keys are left to the caller.
+constexpr int kBigThreads = 1024;
+constexpr uint64_t kBigSegMax = 1ull << 22;
+
+template <int KW>
+__global__ void __launch_bounds__(kBigThreads, 1) big_segment_sort_kernel(
+    uint64_t *data, uint64_t *alt, int bits, const unsigned long long *big,
+    const unsigned long long *nbig) {
+    constexpr int NW = kBigThreads / 32;
+    __shared__ unsigned hist[kRadixBins];
+    __shared__ unsigned long long gbase[kRadixBins];
+    __shared__ uint16_t wcnt[NW][kRadixBins];
+    const unsigned long long seg = blockIdx.x;
+    if (seg >= *nbig) return;
+    const uint64_t begin = big[2 * seg], n = big[2 * seg + 1];
+    if (n > kBigSegMax) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t t0 = top_bits<KW>(data + begin * KW, bits);
+    const uint32_t t1 = top_bits<KW>(data + (begin + n - 1) * KW, bits);
+    const int low = t0 == t1 ? bits - kTopBits : bits;
+    const int passes = (low + kRadixBits - 1) / kRadixBits;
+    uint64_t *src = data + begin * KW, *dst = alt + begin * KW;
+    const unsigned lt = (1u << lane) - 1;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = p * kRadixBits;
+        for (int d = tid; d < kRadixBins; d += kBigThreads) hist[d] = 0;
+        __syncthreads();
+        for (uint64_t i = tid; i < n; i += kBigThreads) atomicAdd(&hist[digit_of<KW>(src + i * KW, shift)], 1u);
+        __syncthreads();
+        if (tid < 32) {   // exclusive scan of the 256 counts by one warp, 8 per lane
+            unsigned v[kRadixBins / 32], sum = 0;
+#pragma unroll
+            for (int j = 0; j < kRadixBins / 32; ++j) {
+                v[j] = hist[lane * (kRadixBins / 32) + j];
+                sum += v[j];
+            }
+            unsigned incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            unsigned long long pre = incl - sum;
+#pragma unroll
+            for (int j = 0; j < kRadixBins / 32; ++j) {
+                gbase[lane * (kRadixBins / 32) + j] = pre;
+                pre += v[j];
+            }
+        }
+        __syncthreads();
+        for (uint64_t t = 0; t < n; t += kBigThreads) {
+            const uint64_t i = t + tid;
+            const bool in = i < n;
+            uint64_t key[KW];
+#pragma unroll
+            for (int w = 0; w < KW; ++w) key[w] = in ? src[i * KW + w] : 0;
+            const unsigned dg = in ? digit_of<KW>(key, shift) : kRadixBins - 1;
+            unsigned peers = __ballot_sync(0xffffffffu, in);
+#pragma unroll
+            for (int b = 0; b < kRadixBits; ++b) {
+                const bool bit = (dg >> b) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bal : ~bal;
+            }
+            for (int d = lane; d < kRadixBins; d += 32) wcnt[warp][d] = 0;
+            __syncwarp();
+            if (in && lane == __ffs(peers) - 1) wcnt[warp][dg] = (uint16_t)__popc(peers);
+            __syncthreads();
+            // per digit: keys of the warps before each warp (in place), and the
+            // digit's count in this tile
+            if (tid < kRadixBins) {
+                unsigned run = 0;
+#pragma unroll 4
+                for (int w = 0; w < NW; ++w) {
+                    const unsigned c = wcnt[w][tid];
+                    wcnt[w][tid] = (uint16_t)run;
+                    run += c;
+                }
+                hist[tid] = run;
+            }
+            __syncthreads();
+            if (in) {
+                const uint64_t o = gbase[dg] + wcnt[warp][dg] + __popc(peers & lt);
+#pragma unroll
+                for (int w = 0; w < KW; ++w) dst[o * KW + w] = key[w];
+            }
+            __syncthreads();
+            if (tid < kRadixBins) gbase[tid] += hist[tid];
+            __syncthreads();
+        }
+        uint64_t *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (passes & 1) {   // the result is in alt: back into place
+        __syncthreads();
+        for (uint64_t i = tid; i < n * KW; i += kBigThreads) data[begin * KW + i] = alt[begin * KW + i];
+    }
 }
 
 uint32_t sort_tiles(uint64_t n, int kw) {
@@ -881,6 +989,20 @@ cudaError_t top_segment_sort(uint64_t *data, uint64_t n, int kw, int bits, unsig
     }
     return cudaGetLastError();
 }
+
+cudaError_t big_segment_sort(uint64_t *data, uint64_t *alt, uint64_t n, int kw, int bits,
+                             const unsigned long long *big, const unsigned long long *nbig,
+                             cudaStream_t s) {
+    // at most one segment per seg_cap keys; blocks past *nbig return at once
+    const uint64_t most = n / (uint64_t)(kw == 1 ? seg_cap<1>() : seg_cap<2>()) + 1;
+    if (kw == 1)
+        big_segment_sort_kernel<1><<<(unsigned)most, kBigThreads, 0, s>>>(data, alt, bits, big, nbig);
+    else
+        big_segment_sort_kernel<2><<<(unsigned)most, kBigThreads, 0, s>>>(data, alt, bits, big, nbig);
+    return cudaGetLastError();
+}
+
+uint64_t big_segment_max() { return kBigSegMax; }
 
 cudaError_t radix_sort(const uint64_t *in, uint64_t *alt0, uint64_t *alt1, uint64_t n, int kw,
                        int bits, uint32_t *counts, const uint64_t **result, cudaStream_t s) {

@@ -381,6 +381,12 @@ cudaError_t radix_pass(const uint64_t *src, uint64_t *dst, uint64_t n, int kw, i
 // Needs 2K >= kTopSortBits + 12.
 constexpr int kTopSortBits = 24;
 uint64_t seg_bounds_entries(uint64_t n, int kw);
+// The big segments of top_segment_sort up to big_segment_max() keys, one
+// block each, sorted in place (alt: scratch of the same layout as data).
+cudaError_t big_segment_sort(uint64_t *data, uint64_t *alt, uint64_t n, int kw, int bits,
+                             const unsigned long long *big, const unsigned long long *nbig,
+                             cudaStream_t s);
+uint64_t big_segment_max();
 cudaError_t top_segment_sort(uint64_t *data, uint64_t n, int kw, int bits, unsigned long long *b,
                              unsigned long long *big, unsigned long long *nbig, cudaStream_t s);
 

@@ -44,13 +44,15 @@ def _exact(bf, b, o, K, m, alpha, nhash, tau):
 ONE = readsim.from_strings(["ACGTTGCATTGACCAGTAGGA"])
 
 
-@pytest.mark.parametrize("mode", [kc.UPDATE_ATOMIC, kc.UPDATE_PARTITIONED])
-def test_retry_limit_reports_timeout_and_reset_recovers(mode):
+@pytest.mark.parametrize("mode,alpha", [(kc.UPDATE_ATOMIC, 4), (kc.UPDATE_PARTITIONED, 4),
+                                        (kc.UPDATE_PARTITIONED, 16)])
+def test_retry_limit_reports_timeout_and_reset_recovers(mode, alpha):
     # 20,000 windows of random bases: the distinct set is sized for them at
     # load factor 1/2, so many inserts need more than one probe past their
-    # home slot; with a limit of one the probe loop gives up
+    # home slot; with a limit of one the probe loop gives up.  (16-bit
+    # counters take the compare-and-swap apply with the handle's bound.)
     b, o = readsim.random_reads(200, 120, 120, seed=91)
-    with kc.CountBF(21, 1 << 20, 4, 4, 2, update_mode=mode, retry_limit=1) as bf:
+    with kc.CountBF(21, 1 << 20, alpha, 4, 2, update_mode=mode, retry_limit=1) as bf:
         bf.insert(_dev(b), _dev(o))
         with pytest.raises(kc.KmercoError) as e:
             bf.classify()
@@ -61,7 +63,7 @@ def test_retry_limit_reports_timeout_and_reset_recovers(mode):
         bf.reset()
         ob, oo = ONE
         bf.insert(_dev(ob), _dev(oo))
-        _exact(bf, ob, oo, 21, 1 << 20, 4, 4, 2)
+        _exact(bf, ob, oo, 21, 1 << 20, alpha, 4, 2)
 
 
 def test_counter_retry_limit_on_one_hot_counter():
