@@ -13,9 +13,12 @@ timed after it and reported under "secondary".
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload repeats]
     python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
-Under torchrun (N > 1) every rank counts its own sample (a different seed)
-on its own GPU; nothing is exchanged, so scaling is weak and value is the sum
-of all ranks' windows over the slowest rank's time.
+Under torchrun (N > 1) the ranks count ONE sample together: rank r inserts
+read shard r, the countBFs are merged with a chunked all-to-all and a
+saturating merge, and the distinct keys go to the rank owning their key range
+(scaling "strong": value = the sample's windows over the slowest rank's
+time).  With --replicas every rank counts its own sample instead (scaling
+"weak").
 """
 from __future__ import annotations
 
@@ -159,6 +162,28 @@ def measure_peaks(device: int) -> dict:
     for name, nbytes in (("512KiB", 512 << 10), ("128MiB", 128 << 20), ("4GiB", 4 << 30)):
         out[name] = {"random_cas_per_s": kc.kmerco_peak_random_cas(nbytes, 1 << 28, device),
                      "random_read_per_s": kc.kmerco_peak_random_read(nbytes, 1 << 28, device)}
+    return out
+
+
+def host_link(device: int) -> dict:
+    """Pinned host <-> device copy rates of 1 GiB (CUDA events): the link the
+    end-to-end number moves its reads and results over."""
+    import torch
+    n = 1 << 30
+    h = torch.empty(n, dtype=torch.uint8).pin_memory()
+    d = torch.empty(n, dtype=torch.uint8, device=device)
+    out = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 3 * n / (e0.elapsed_time(e1) / 1000.0) / 1e9
+    del h, d
     return out
 
 
@@ -465,6 +490,74 @@ def workload_roofline(r: dict, name: str, input_bytes: int, peak: float, peak_sr
     return roof
 
 
+def run_sharded(args) -> None:
+    """N > 1 ranks count ONE sample: rank r inserts read shard r into a
+    full-size countBF, the countBFs are merged by a chunked all-to-all with a
+    saturating merge and gathered back, and the distinct keys go to the rank
+    owning their key range (paper_2305_07545_gb300.shard).  The total work is
+    fixed, so the scaling is strong."""
+    import torch
+    import torch.distributed as dist
+    from paper_2305_07545_gb300 import shard
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    name = args.workload
+    w = readsim.WORKLOADS[name]
+    wl = readsim.scaled(name, args.reads or w.reads.n_reads)   # the same sample on every rank
+    bases, offsets = wl.generate()
+    dev = torch.cuda.current_device()
+    sb, so = shard.shard_of(bases, offsets, rank, world)
+    d_shard = (torch.from_numpy(sb).to(dev), torch.from_numpy(so.view(np.int64)).to(dev))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    comm = shard.TorchComm()
+    eng = shard.LibraryEngine(w.K, args.counters or w.m, w.alpha, w.nhash, w.tau, device=dev)
+
+    def step():
+        eng.local.reset()
+        res = shard.count_sharded(eng, comm, shard=d_shard)
+        res.owner.close()
+        return res
+
+    for _ in range(args.warmup):
+        res = step()
+    times = []
+    torch.cuda.synchronize()
+    dist.barrier()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            res = step()
+            torch.cuda.synchronize()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    total_ms = max_over_ranks(sum(times), dev)
+    dist.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": res.inserted * args.steps / (total_ms / 1000.0),
+                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": describe(wl), "K": w.K, "m": args.counters or w.m,
+                           "kmers_per_step": res.inserted, "distinct": res.distinct,
+                           "trustworthy": res.trustworthy,
+                           "parallelism": f"one sample sharded over {world} GPUs: read shards, "
+                                          "countBF chunks all-to-all + saturating merge + "
+                                          "all-gather, distinct keys all-to-all by key range",
+                           "l2": "256 MiB buffer written between timed steps"},
+                "gpu_launches": None, "clocks": clk.summary(),
+                "note": "wall time of the whole sharded step between device synchronisations, "
+                        "timed with CUDA events; slowest rank"}
+        print(json.dumps(line), flush=True)
+    eng.close()
+    dist.destroy_process_group()
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -486,6 +579,7 @@ def run_ours(args) -> None:
     clock_dev = dev if world == 1 else local
 
     peaks = None if args.no_peaks else measure_peaks(dev)
+    link = None if args.no_e2e else host_link(dev)
     d_bases = torch.from_numpy(bases).to(dev)
     d_offsets = torch.from_numpy(offsets.view(np.int64)).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -542,7 +636,8 @@ def run_ours(args) -> None:
                              "per-step CUDA events; inputs and countBF larger than L2",
                        "device_bytes": r["device_bytes"],
                        "read_generation_s": round(t_gen, 1)},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": r["e2e"],
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": dict(r["e2e"], host_link=link) if r["e2e"] else None,
             "phases": {"insert_ms": r["insert_ms"], "classify_ms": r["classify_ms"],
                        "insert_kmers_per_s": r["inserted"] / (r["insert_ms"] / 1000.0),
                        "classify_distinct_per_s": r["distinct"] / (r["classify_ms"] / 1000.0)},
@@ -749,6 +844,9 @@ def main(argv=None) -> None:
                     help="skip the 55-mer count of the same reads after the headline workload")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the random-access peak measurements")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with N > 1: every rank counts its own sample instead of one "
+                         "sample sharded over all ranks")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -758,6 +856,8 @@ def main(argv=None) -> None:
         run_batched(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif dist_setup()[0] > 1 and not args.replicas:
+        run_sharded(args)
     else:
         run_ours(args)
 

@@ -272,6 +272,28 @@ int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est);
 int kmerco_merge(kmerco_t *dst, kmerco_t *src);
 
 /*
+ * Sharded counting (one sample's reads spread over several handles, on one
+ * or several GPUs; the paper counts on one thread, so this is an exchange
+ * step of the GPU schedule, exact by Algorithm 3's per-counter saturation):
+ *
+ * kmerco_merge_cells: counters of cells [first_word, first_word + nwords)
+ *   become min(a + b, 2^alpha - 1) with b the counters of src (host or
+ *   device, nwords cells in the kmerco_get_counters layout, e.g. another
+ *   shard's cells of that range).  Merging every shard's countBF this way
+ *   gives the countBF of all shards' reads.  Synchronises.
+ *   Errors: EINVAL (NULL), ESIZE (range outside the countBF), ECUDA.
+ * kmerco_rank_of: after kmerco_classify, ranks[i] = the number of the
+ *   handle's distinct keys below probes[i] (the lower bound of the probe in
+ *   the ascending distinct list), for n probe keys (host or device, key
+ *   layout as above); ranks is host or device, n uint64.  Cuts the sorted
+ *   distinct keys at key-range splitters when routing them to the shard
+ *   that owns each range.  Synchronises.  Errors: EINVAL, ESTATE (not
+ *   classified), ENOMEM, ECUDA.
+ */
+int kmerco_merge_cells(kmerco_t *h, const uint64_t *src, uint64_t first_word, uint64_t nwords);
+int kmerco_rank_of(kmerco_t *h, const uint64_t *probes, uint64_t n, uint64_t *ranks);
+
+/*
  * Allocation-free classification.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory themselves
  * -- a process whose GPU memory is all reserved up front by its own pool

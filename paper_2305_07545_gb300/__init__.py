@@ -121,6 +121,8 @@ SIGNATURES = {
     "kmerco_batch_classify": (c_int, [c_void_p]),
     "kmerco_batch_schedule": (c_int, [c_void_p, c_int, c_int]),
     "kmerco_batch_info": (c_int, [c_void_p, c_void_p]),
+    "kmerco_merge_cells": (c_int, [c_void_p, c_void_p, c_uint64, c_uint64]),
+    "kmerco_rank_of": (c_int, [c_void_p, c_void_p, c_uint64, c_void_p]),
     "kmerco_estimate_bytes": (c_int, [POINTER(kmerco_config_t), c_uint64, c_uint64, c_uint64, c_int,
                                       _u64p]),
     "kmerco_peak_random_cas": (c_int, [c_uint64, c_uint64, c_int, POINTER(ctypes.c_double)]),
@@ -284,6 +286,14 @@ def kmerco_query(h: int, keys, n: int, est) -> None:
 
 def kmerco_merge(dst: int, src: int) -> None:
     _check(load().kmerco_merge(dst, src), "kmerco_merge")
+
+
+def kmerco_merge_cells(h: int, src, first_word: int, nwords: int) -> None:
+    _check(load().kmerco_merge_cells(h, _ptr(src), first_word, nwords), "kmerco_merge_cells")
+
+
+def kmerco_rank_of(h: int, probes, n: int, ranks) -> None:
+    _check(load().kmerco_rank_of(h, _ptr(probes), n, _ptr(ranks)), "kmerco_rank_of")
 
 
 def kmerco_set_counters(h: int, src, nwords: int) -> None:

@@ -43,6 +43,7 @@ struct kmerco {
     DevCounters *ctr_host;   // pinned mirror
     uint64_t *table;         // distinct-key set: cap slots of kw words
     uint64_t cap;
+    uint32_t gen;            // generation tag of the set's current keys
     uint64_t *dlist;         // distinct keys in arrival order
     uint64_t dlist_cap;
     uint64_t d_ub;           // upper bound of the distinct keys held
@@ -205,6 +206,24 @@ int read_counters(kmerco_t *h) {
     return KMERCO_OK;
 }
 
+// Generation tag of the handle's distinct set: the spare bits above the key
+// in a slot's top word (2K key bits; two-word keys keep 2K - 64 of them in
+// the top word).  Fewer than two spare bits: no tag, free slots are all ones.
+SetTag set_tag(const kmerco_t *h) {
+    const int used = h->kw == 1 ? 2 * h->K : 2 * h->K - 64;
+    const int spare = 64 - used;
+    if (spare < 2) return SetTag{0, 0};
+    return SetTag{(uint64_t)h->gen << used, (~0ull >> used) << used};
+}
+
+// Generations the tag can tell apart (the all-ones tag is left to cleared
+// slots), or 0 without a tag.
+uint32_t tag_count(const kmerco_t *h) {
+    const int spare = 64 - (h->kw == 1 ? 2 * h->K : 2 * h->K - 64);
+    if (spare < 2) return 0;
+    return spare >= 32 ? 0xFFFFFFFFu : (1u << spare) - 1;
+}
+
 int device_error_status(unsigned err) {
     if (err & kErrListFull) return KMERCO_ENOMEM;
     if (err & (kErrCasLimit | kErrProbeLimit)) return KMERCO_ETIMEOUT;
@@ -249,8 +268,8 @@ int ensure_set_capacity(kmerco_t *h, uint64_t add) {
         KM_TRY(dev_alloc(h, &q, want * h->kw * 8));
         KM_CUDA(cudaMemsetAsync(q, 0xFF, want * h->kw * 8, h->stream));
         KM_CUDA(launch_reinsert(h->dlist, D < h->dlist_cap ? D : h->dlist_cap, h->kw,
-                                (uint64_t *)q, want, nullptr, 0, h->ctr, h->G.probe_limit,
-                                h->stream));
+                                (uint64_t *)q, want, set_tag(h), nullptr, 0, h->ctr,
+                                h->G.probe_limit, h->stream));
         h->launches += D ? 1 : 0;
         KM_CUDA(cudaStreamSynchronize(h->stream));
         dev_free(h, h->table, h->cap * h->kw * 8);
@@ -405,6 +424,7 @@ InsertArgs sample_args(const kmerco_t *h, const uint8_t *d_bases, const uint64_t
     a.G = h->G;
     a.table = h->table;
     a.cap = h->cap;
+    a.set_tag = set_tag(h);
     a.dlist = h->dlist;
     a.dlist_cap = h->dlist_cap;
     a.ctr = h->ctr;
@@ -751,7 +771,16 @@ int kmerco_reset(kmerco_t *h) {
     if (!h) return KMERCO_EINVAL;
     DeviceGuard guard(h->device);
     KM_CUDA(cudaMemsetAsync(h->G.cells, 0, h->G.words * 8, h->stream));
-    if (h->table && h->d_ub) KM_CUDA(cudaMemsetAsync(h->table, 0xFF, h->cap * h->kw * 8, h->stream));
+    if (h->table && h->d_ub) {
+        // the next generation tag makes every held key read as a free slot;
+        // once the tags run out the table is cleared and they start again
+        if (h->gen + 1 < tag_count(h)) {
+            ++h->gen;
+        } else {
+            KM_CUDA(cudaMemsetAsync(h->table, 0xFF, h->cap * h->kw * 8, h->stream));
+            h->gen = 0;
+        }
+    }
     KM_CUDA(cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->stream));
     h->d_ub = 0;
     h->classified = false;
@@ -1075,8 +1104,8 @@ int kmerco_add_distinct(kmerco_t *h, const uint64_t *keys, uint64_t n) {
         d_keys = h->alt0;
     }
     KM_TRY(ensure_set_capacity(h, n));
-    KM_CUDA(launch_reinsert(d_keys, n, h->kw, h->table, h->cap, h->dlist, h->dlist_cap, h->ctr,
-                            h->G.probe_limit, h->stream));
+    KM_CUDA(launch_reinsert(d_keys, n, h->kw, h->table, h->cap, set_tag(h), h->dlist,
+                            h->dlist_cap, h->ctr, h->G.probe_limit, h->stream));
     h->launches += 1;
     KM_TRY(read_counters(h));
     KM_TRY(device_error_status(h->ctr_host->error));
@@ -1157,6 +1186,63 @@ int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est) {
     return KMERCO_OK;
 }
 
+int kmerco_merge_cells(kmerco_t *h, const uint64_t *src, uint64_t first_word, uint64_t nwords) {
+    Range range("kmerco_merge_cells");
+    if (!h || (!src && nwords)) return KMERCO_EINVAL;
+    if (first_word > h->G.words || nwords > h->G.words - first_word) return KMERCO_ESIZE;
+    if (nwords == 0) return KMERCO_OK;
+    DeviceGuard guard(h->device);
+    const uint64_t *d_src = src;
+    if (!is_device_ptr(src)) {   // host words: staged in the classification buffer
+        KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, nwords));
+        KM_CUDA(cudaMemcpyAsync(h->alt0, src, nwords * 8, cudaMemcpyHostToDevice, h->stream));
+        d_src = h->alt0;
+    }
+    Geometry part = h->G;   // the same counters, over words [first_word, first_word + nwords)
+    part.cells = h->G.cells + first_word;
+    part.words = nwords;
+    KM_CUDA(launch_merge(part.cells, d_src, part, h->stream));
+    h->launches += 1;
+    KM_CUDA(cudaStreamSynchronize(h->stream));
+    h->classified = false;
+    return KMERCO_OK;
+}
+
+int kmerco_rank_of(kmerco_t *h, const uint64_t *probes, uint64_t n, uint64_t *ranks) {
+    if (!h || (n && (!probes || !ranks))) return KMERCO_EINVAL;
+    if (!h->classified) return KMERCO_ESTATE;
+    if (n == 0) return KMERCO_OK;
+    DeviceGuard guard(h->device);
+    const int kw = h->kw;
+    // probes and ranks through the query staging buffer (kw words in, one
+    // word out per probe; the buffer holds two words per slot)
+    const uint64_t slots = (n * (uint64_t)(kw + 1) + 1) / 2;
+    if (!h->q_keys || h->q_cap < slots) {
+        dev_free(h, h->q_keys, h->q_cap * 16);
+        dev_free(h, h->q_est, h->q_cap * 4);
+        h->q_keys = nullptr;
+        h->q_est = nullptr;
+        h->q_cap = 0;
+        void *p;
+        KM_TRY(dev_alloc(h, &p, slots * 16));
+        h->q_keys = (uint64_t *)p;
+        if (dev_alloc(h, &p, slots * 4) != KMERCO_OK) {
+            dev_free(h, h->q_keys, slots * 16);
+            h->q_keys = nullptr;
+            return KMERCO_ENOMEM;
+        }
+        h->q_est = (uint32_t *)p;
+        h->q_cap = slots;
+    }
+    KM_CUDA(cudaMemcpyAsync(h->q_keys, probes, n * kw * 8, cudaMemcpyDefault, h->stream));
+    uint64_t *d_ranks = h->q_keys + n * kw;
+    KM_CUDA(launch_lower_bound(h->sorted, h->n_distinct, kw, h->q_keys, n, d_ranks, h->stream));
+    h->launches += 1;
+    KM_CUDA(cudaMemcpyAsync(ranks, d_ranks, n * 8, cudaMemcpyDefault, h->stream));
+    KM_CUDA(cudaStreamSynchronize(h->stream));
+    return KMERCO_OK;
+}
+
 int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
     Range range("kmerco_merge");
     if (!dst || !src || dst == src) return KMERCO_EINVAL;
@@ -1170,8 +1256,9 @@ int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
     const DevCounters sc = *src->ctr_host;
     KM_TRY(ensure_set_capacity(dst, sc.distinct));
     KM_CUDA(launch_merge(dst->G.cells, src->G.cells, dst->G, dst->stream));
-    KM_CUDA(launch_reinsert(src->dlist, sc.distinct, dst->kw, dst->table, dst->cap, dst->dlist,
-                            dst->dlist_cap, dst->ctr, dst->G.probe_limit, dst->stream));
+    KM_CUDA(launch_reinsert(src->dlist, sc.distinct, dst->kw, dst->table, dst->cap,
+                            set_tag(dst), dst->dlist, dst->dlist_cap, dst->ctr,
+                            dst->G.probe_limit, dst->stream));
     dst->launches += sc.distinct ? 2 : 1;
     KM_TRY(read_counters(dst));
     DevCounters dc = *dst->ctr_host;
@@ -1205,6 +1292,7 @@ struct kmerco_batch {
     std::vector<unsigned long long> chunk_end, bound_host;
     std::vector<const char *> p_bases;       // inputs of the planned launch
     std::vector<const uint64_t *> p_offs;
+    std::vector<uint32_t> graph_gen;         // distinct-set generation of each handle at capture
     std::vector<uint64_t> p_nreads;
     bool planned, tuned, have_graph;
     int chunk, bpm;
@@ -1262,6 +1350,7 @@ int batch_build_args(kmerco_batch *b, int chunk) {
         a.G = h->G;
         a.table = h->table;
         a.cap = h->cap;
+        a.set_tag = set_tag(h);
         a.dlist = h->dlist;
         a.dlist_cap = h->dlist_cap;
         a.ctr = h->ctr;
@@ -1477,7 +1566,8 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
     // the same inputs as the captured launch: replay the graph
     bool same = b->planned && reset && b->have_graph;
     for (int i = 0; same && i < b->n; ++i)
-        same = b->p_bases[i] == bases[i] && b->p_offs[i] == offsets[i] && b->p_nreads[i] == nreads[i];
+        same = b->p_bases[i] == bases[i] && b->p_offs[i] == offsets[i] &&
+               b->p_nreads[i] == nreads[i] && b->h[i]->gen == b->graph_gen[i];
     if (same) {
         KM_CUDA(cudaGraphLaunch(b->exec, b->stream));
         b->launches += b->total_chunks ? 2 : 0;
@@ -1600,6 +1690,8 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
             }
             b->graph = g;
             b->have_graph = true;
+            b->graph_gen.resize(b->n);   // the tags the graph's launches carry
+            for (int i = 0; i < b->n; ++i) b->graph_gen[i] = b->h[i]->gen;
             KM_CUDA(cudaGraphLaunch(b->exec, b->stream));
         }
     } else {

@@ -1063,6 +1063,34 @@ cudaError_t launch_split(const uint64_t *keys, const uint32_t *est, uint64_t n, 
     return cudaGetLastError();
 }
 
+// pos[i] = number of keys of the sorted array below probe i (lower bound).
+template <int KW>
+__global__ void lower_bound_kernel(const uint64_t *keys, uint64_t n, const uint64_t *probes,
+                                   uint64_t np, uint64_t *pos) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (key_less<KW>(keys + mid * KW, probes + i * KW))
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    pos[i] = lo;
+}
+
+cudaError_t launch_lower_bound(const uint64_t *keys, uint64_t n, int kw, const uint64_t *probes,
+                               uint64_t np, uint64_t *pos, cudaStream_t s) {
+    if (np == 0) return cudaSuccess;
+    const unsigned g = (unsigned)((np + 255) / 256);
+    if (kw == 1)
+        lower_bound_kernel<1><<<g, 256, 0, s>>>(keys, n, probes, np, pos);
+    else
+        lower_bound_kernel<2><<<g, 256, 0, s>>>(keys, n, probes, np, pos);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_merge(uint64_t *dst, const uint64_t *src, Geometry G, cudaStream_t s) {
     merge_kernel<<<grid_for(G.words, 256, 152 * 16), 256, 0, s>>>(dst, src, G);
     return cudaGetLastError();

@@ -133,31 +133,55 @@ __device__ __forceinline__ void sat_increment(uint64_t *cells, uint64_t c, unsig
 }
 
 // Insert a key into the distinct set; true when the key was not there yet.
+// A slot stores the key with the set's generation tag in the unused top bits
+// of its top word (SetTag): a slot whose tag differs from the current one is
+// free, so a reset only moves to the next tag instead of clearing the table.
+// Without spare bits (mask 0) a free slot is all ones, cleared at reset.
 // For one-word keys `first` is an already loaded value of the home slot
-// (kEmptyKey - 1 when none was loaded, a value no key or empty slot has).
+// (kEmptyKey - 1 when none was loaded, a value no slot holds).
+__device__ __forceinline__ bool slot_free(uint64_t top, const SetTag &t) {
+    return t.mask ? (top & t.mask) != t.tag : top == kEmptyKey;
+}
+
 template <int KW>
 __device__ __forceinline__ bool set_insert(uint64_t *table, uint64_t cap, uint64_t th,
-                                           uint64_t klo, uint64_t khi, uint32_t limit,
-                                           unsigned *err, uint64_t pol,
+                                           uint64_t klo, uint64_t khi, const SetTag &t,
+                                           uint32_t limit, unsigned *err, uint64_t pol,
                                            uint64_t first = kEmptyKey - 1) {
     uint64_t slot = __umul64hi(th, cap);
     for (uint32_t it = 0;; ++it) {
         if (KW == 1) {
+            const uint64_t want = klo | t.tag;
             uint64_t v = (it == 0 && first != kEmptyKey - 1) ? first : load_hint(table + slot, pol);
-            if (v == klo) return false;
-            if (v == kEmptyKey) {
-                uint64_t prev = atomicCAS((unsigned long long *)(table + slot),
-                                          (unsigned long long)kEmptyKey, (unsigned long long)klo);
-                if (prev == kEmptyKey) return true;
-                if (prev == klo) return false;
+            for (;;) {   // settle this slot
+                if (v == want) return false;
+                if (!slot_free(v, t)) break;   // another key
+                const uint64_t prev = atomicCAS((unsigned long long *)(table + slot),
+                                                (unsigned long long)v, (unsigned long long)want);
+                if (prev == v) return true;
+                v = prev;                      // written meanwhile: look again
             }
         } else {
-            // 16-byte slots are only ever read through the atomic itself, so
-            // a half-written slot is never mistaken for a key.
-            uint64_t olo, ohi;
-            cas128(table + 2 * slot, kEmptyKey, kEmptyKey, klo, khi, olo, ohi);
-            if (olo == kEmptyKey && ohi == kEmptyKey) return true;
-            if (olo == klo && ohi == khi) return false;
+            // A plain 16-byte load settles most probes without an atomic: the
+            // key itself, or another key (a different top word: each slot is
+            // written once per generation).  A free slot, or one showing our
+            // top word with another low word (a different key, or ours half
+            // written), is decided by the 128-bit compare-and-swap, whose
+            // result is the slot's real contents.
+            const uint64_t whi = khi | t.tag;
+            ulonglong2 v = __ldcg((const ulonglong2 *)(table + 2 * slot));
+            for (;;) {
+                if (v.x == klo && v.y == whi) return false;
+                const bool free = t.mask ? slot_free(v.y, t) : (v.x == kEmptyKey || v.y == kEmptyKey);
+                if (!free && v.y != whi) break;
+                const uint64_t elo = free ? v.x : kEmptyKey, ehi = free ? v.y : kEmptyKey;
+                uint64_t olo, ohi;
+                cas128(table + 2 * slot, elo, ehi, klo, whi, olo, ohi);
+                if (olo == elo && ohi == ehi) return true;
+                if (!free && olo == v.x && ohi == v.y) break;   // a different key, settled
+                v.x = olo;
+                v.y = ohi;
+            }
         }
         if (++slot == cap) slot = 0;
         if (it >= limit) {
@@ -443,8 +467,8 @@ __device__ __forceinline__ void process_chunk(const InsertArgs &a, uint64_t chun
 
         bool isnew = false;
         if (active)
-            isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, G.probe_limit,
-                                   &a.ctr->error, pol_stream, table_first);
+            isnew = set_insert<KW>(a.table, a.cap, table_hash, klo, khi, a.set_tag,
+                                   G.probe_limit, &a.ctr->error, pol_stream, table_first);
         const unsigned bal = __ballot_sync(0xffffffffu, isnew);
         unsigned base = 0;
         if (lane == 0 && bal) base = atomicAdd(&S.nfresh, (unsigned)__popc(bal));
@@ -706,7 +730,7 @@ __global__ void first_read_batch_kernel(const InsertArgs *args, const unsigned l
 // handle's keys).  With dlist != nullptr keys new to the set are appended.
 template <int KW>
 __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *table, uint64_t cap,
-                                uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
+                                SetTag tag, uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
                                 uint32_t probe_limit) {
     const int lane = threadIdx.x & 31;
     for (uint64_t i0 = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) & ~31ull; i0 < n;
@@ -722,7 +746,7 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
                 murmur8(premix8(klo), 0, h1, h2);
             else
                 murmur16(klo, khi, 0, h1, h2);
-            isnew = set_insert<KW>(table, cap, h2, klo, khi, probe_limit, &ctr->error,
+            isnew = set_insert<KW>(table, cap, h2, klo, khi, tag, probe_limit, &ctr->error,
                                    policy_stream());
         }
         if (dlist) {
@@ -1157,17 +1181,17 @@ cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s) {
 }
 
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,
-                            uint64_t cap, uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
-                            uint32_t probe_limit, cudaStream_t s) {
+                            uint64_t cap, SetTag tag, uint64_t *dlist, uint64_t dlist_cap,
+                            DevCounters *ctr, uint32_t probe_limit, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     uint64_t blocks = (n + 255) / 256;
     if (blocks > 65536) blocks = 65536;
     if (kw == 1)
-        reinsert_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr,
-                                                             probe_limit);
+        reinsert_kernel<1><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, tag, dlist, dlist_cap,
+                                                             ctr, probe_limit);
     else
-        reinsert_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, dlist, dlist_cap, ctr,
-                                                             probe_limit);
+        reinsert_kernel<2><<<(unsigned)blocks, 256, 0, s>>>(keys, n, table, cap, tag, dlist, dlist_cap,
+                                                             ctr, probe_limit);
     return cudaGetLastError();
 }
 

@@ -274,6 +274,14 @@ __device__ __forceinline__ void revcomp128(uint64_t hi, uint64_t lo, int K, uint
     }
 }
 
+// Generation tag of a distinct set: `tag` in the `mask` bits of a slot's
+// top word (the bits above the key); mask 0 when the key leaves fewer than
+// two spare bits (a free slot is then all ones).
+struct SetTag {
+    uint64_t tag;
+    uint64_t mask;
+};
+
 // ------------------------------------------------------------- launchers
 struct InsertArgs {
     const uint8_t *bases;        // points at absolute position `first`
@@ -289,6 +297,7 @@ struct InsertArgs {
     Geometry G;
     uint64_t *table;             // distinct-key set, cap slots of kw words
     uint64_t cap;
+    SetTag set_tag;              // current generation of the set
     uint64_t *dlist;             // distinct keys in arrival order
     uint64_t dlist_cap;
     DevCounters *ctr;
@@ -359,8 +368,8 @@ cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_
 // Insert n keys into a distinct set; when dlist is not null, keys new to the
 // set are appended to it (ctr->distinct counts them).
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,
-                            uint64_t cap, uint64_t *dlist, uint64_t dlist_cap, DevCounters *ctr,
-                            uint32_t probe_limit, cudaStream_t s);
+                            uint64_t cap, SetTag tag, uint64_t *dlist, uint64_t dlist_cap,
+                            DevCounters *ctr, uint32_t probe_limit, cudaStream_t s);
 
 // Radix sort of n keys of kw words (1 or 2) on their low `bits` bits.  The
 // sorted keys end in *result, which is one of in, alt0 or alt1; in is left
@@ -417,6 +426,9 @@ cudaError_t launch_split(const uint64_t *keys, const uint32_t *est, uint64_t n, 
                          uint32_t tau, uint64_t *out, uint64_t *scratch, DevCounters *ctr,
                          cudaStream_t s);
 cudaError_t launch_merge(uint64_t *dst, const uint64_t *src, Geometry G, cudaStream_t s);
+// pos[i] = lower bound of probe i (kw words) in n sorted keys.
+cudaError_t launch_lower_bound(const uint64_t *keys, uint64_t n, int kw, const uint64_t *probes,
+                               uint64_t np, uint64_t *pos, cudaStream_t s);
 
 cudaError_t launch_count_saturated(Geometry G, DevCounters *ctr, cudaStream_t s);
 

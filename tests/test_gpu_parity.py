@@ -324,6 +324,31 @@ def test_reset_reuse_and_states():
         assert np.array_equal(bf.distinct()[0], first[1])
 
 
+@pytest.mark.parametrize("K,mode", [(21, kc.UPDATE_AUTO), (31, kc.UPDATE_PARTITIONED),
+                                    (32, kc.UPDATE_ATOMIC), (55, kc.UPDATE_PARTITIONED)])
+def test_reset_generations(K, mode):
+    # a reset moves the distinct set to its next generation tag instead of
+    # clearing it (K = 31 has three tags, so the fourth reset clears the
+    # table; K = 32 has no spare bits and clears every time): each sample
+    # counted after a reset must see none of the earlier samples' keys
+    with kc.CountBF(K, 1 << 22, 4, 3, 2, update_mode=mode) as bf:
+        for i in range(6):
+            b, o = readsim.scaled("tiny", 400 + 150 * (i % 3), seed_offset=300 + i).generate()
+            if i:
+                bf.reset()
+            bf.insert(_dev(b), _dev(o))
+            if i == 2:   # a second insert on top, then more keys added by hand
+                b2, o2 = readsim.scaled("tiny", 200, seed_offset=399).generate()
+                bf.insert(_dev(b2), _dev(o2))
+                b = np.concatenate([b, b2])
+                o = np.concatenate([o, o2[1:] + o[-1]])
+            bf.classify()
+            keys, est = bf.distinct()
+            g = dict(stats=bf.stats(), counters=bf.counters(), keys=keys, est=est,
+                     trusted=bf.trusted(), erroneous=bf.erroneous())
+            check(g, b, o, K, 4, 3, 2)
+
+
 def test_empty_and_too_short_inputs():
     for reads in ([], [""], ["ACGT", "AC", ""], ["N" * 50]):
         b, o = readsim.from_strings(reads)
