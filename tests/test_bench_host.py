@@ -48,3 +48,12 @@ def test_traffic_records_are_well_formed():
         assert len(kv["source_sha"]) == 16 and int(kv["source_sha"], 16) >= 0
         assert float(kv["dram_bytes_per_launch"]) > 0
     assert len(bench.source_sha()) == 16
+
+
+def test_batch_groups_respect_the_memory_limit():
+    sizes = [5, 5, 5, 20, 1, 1, 9]
+    groups = bench.batch_groups(sizes, 10)
+    assert [i for g in groups for i in g] == list(range(len(sizes)))   # every sample once, in order
+    for g in groups:
+        assert len(g) == 1 or sum(sizes[i] for i in g) <= 10
+    assert bench.batch_groups(sizes, 1000) == [list(range(len(sizes)))]
