@@ -429,7 +429,7 @@ def time_workload(name: str, args, bases, offsets, d_bases, d_offsets, flush, cl
         h_tr = torch.empty(cap * kw, dtype=torch.int64).pin_memory()
         h_er = torch.empty(cap * kw, dtype=torch.int64).pin_memory()
 
-        split = {"reset_insert": 0.0, "classify": 0.0, "copy_back": 0.0}
+        split = {"reset_insert": 0.0, "classify": 0.0, "copy_back": 0.0, "copy_trusted": 0.0}
 
         def e2e_step():
             t = time.perf_counter()
@@ -439,11 +439,13 @@ def time_workload(name: str, args, bases, offsets, d_bases, d_offsets, flush, cl
             bf.classify()   # waits for the insert (it reads the distinct count)
             t2 = time.perf_counter()
             nt = kc.kmerco_get_trusted(bf.h, h_tr, cap)
+            t25 = time.perf_counter()
             ne = kc.kmerco_get_erroneous(bf.h, h_er, cap)
             t3 = time.perf_counter()
             split["reset_insert"] += t1 - t
             split["classify"] += t2 - t1
             split["copy_back"] += t3 - t2
+            split["copy_trusted"] += t25 - t2
             return nt, ne
 
         for _ in range(max(1, args.warmup // 2)):

@@ -889,8 +889,10 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
 // apply its increment codes with shared-memory compare-and-swap (saturating
 // at 2^alpha - 1), write it back.  LIMITED takes the retry bound from the
 // handle (a retry limit set for testing); the default bound is a constant,
-// which keeps the retry loop measurably faster.
-template <bool LIMITED>
+// which keeps the retry loop measurably faster.  With HALF (alpha divides
+// 32, so no counter straddles the middle of a cell) each update is a 32-bit
+// compare-and-swap on the half-cell that holds the counter.
+template <bool LIMITED, bool HALF>
 __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
     extern __shared__ unsigned long long cells_s[];
     const uint64_t s = blockIdx.x;
@@ -934,6 +936,22 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
             if (!((valid >> q) & 1u)) continue;   // past the end
             const unsigned w = (code[q] >> 6) & wmask;
             const unsigned shift = (code[q] & 63u) * alpha;
+            if (HALF) {   // the little-endian half-cell holding the counter
+                unsigned *h32 = (unsigned *)cells_s + 2 * w + (shift >> 5);
+                const unsigned sh = shift & 31u, mc = (unsigned)maxc;
+                unsigned old = *h32;
+                for (uint32_t it = 0;; ++it) {
+                    if (((old >> sh) & mc) == mc) break;
+                    const unsigned prev = atomicCAS(h32, old, old + (1u << sh));
+                    if (prev == old) break;
+                    old = prev;
+                    if (it >= (LIMITED ? p.G.cas_limit : kCasLimit)) {
+                        atomicOr(&p.ctr->error, kErrCasLimit);
+                        break;
+                    }
+                }
+                continue;
+            }
             unsigned long long old = cells_s[w];
             for (uint32_t it = 0;; ++it) {
                 if (((old >> shift) & maxc) == maxc) break;
@@ -1151,7 +1169,10 @@ cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
     if (nslices == 0) return cudaSuccess;
     if (p.lane_codes || p.cap % 4) return cudaErrorInvalidValue;   // 32-bit codes, 16-byte aligned
     const size_t smem = (size_t)8 << p.slice_shift;
-    void (*k)(ApplyArgs) = p.G.cas_limit == kCasLimit ? apply_kernel<false> : apply_kernel<true>;
+    const bool half = 32 % p.G.alpha == 0;
+    void (*k)(ApplyArgs) = p.G.cas_limit == kCasLimit
+                               ? (half ? apply_kernel<false, true> : apply_kernel<false, false>)
+                               : (half ? apply_kernel<true, true> : apply_kernel<true, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(8 << kSliceShift));
     if (e != cudaSuccess) return e;
