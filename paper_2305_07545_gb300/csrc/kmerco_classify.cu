@@ -605,6 +605,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) bucket_sort_kernel(
 // its own.
 constexpr int kTopBits = kTopSortBits;
 constexpr unsigned kRankMax = 256;   // largest sub-bin rank-sorted in a segment
+constexpr unsigned kMaxLarge = 8;     // larger sub-bins sorted one by one; more: the whole segment
 
 template <int KW>
 __host__ __device__ constexpr int seg_cap() { return KW == 1 ? kBucketCap : kBucketCap / 2; }
@@ -653,7 +654,8 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
     uint64_t *B = (uint64_t *)sm;            // C keys of KW words
     unsigned *hist = (unsigned *)(sm + C * KW);
     unsigned *st = hist + kSubBins, *fill = st + kSubBins;
-    __shared__ unsigned maxsub;
+    __shared__ unsigned maxsub, nlarge;
+    __shared__ unsigned large[kMaxLarge];   // sub-bins above kRankMax keys
     const uint64_t s0 = b[blockIdx.x], e0 = b[blockIdx.x + 1];
     if (e0 <= s0 + 1) return;   // empty or one key
     const uint64_t nn = e0 - s0;
@@ -679,7 +681,10 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
     if (r < 0) r = 0;
     const uint64_t base = (uint64_t)t0 << below;
     for (unsigned i = tid; i < kSubBins; i += kBucketThreads) hist[i] = 0;
-    if (tid == 0) maxsub = 0;
+    if (tid == 0) {
+        maxsub = 0;
+        nlarge = 0;
+    }
     __syncthreads();
     // sub-bin of a key (recomputed where needed: registers hold the keys)
     auto sub_of = [&](const uint64_t *k) {
@@ -709,6 +714,10 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
             st[tid * 4 + j] = pre;
             fill[tid * 4 + j] = pre;
             pre += v[j];
+            if (v[j] > kRankMax) {
+                const unsigned q = atomicAdd(&nlarge, 1u);
+                if (q < kMaxLarge) large[q] = tid * 4 + j;
+            }
         }
         atomicMax(&maxsub, mx);
     }
@@ -722,6 +731,56 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
         }
     }
     __syncthreads();
+    if (maxsub > (unsigned)kRankMax && nlarge <= kMaxLarge) {
+        // a few clustered sub-bins: each sorted in place by the whole block
+        // with a bitonic network for any length (every compare-exchange puts
+        // the smaller key first; a partner past the end stands for +infinity
+        // and is skipped), the others rank sorted as below
+        for (unsigned q = 0; q < nlarge; ++q) {
+            const unsigned a0 = st[large[q]], m = hist[large[q]];
+            uint64_t *X = B + (uint64_t)a0 * KW;
+            unsigned P = 2;
+            while (P < m) P <<= 1;
+            for (unsigned k = 2; k <= P; k <<= 1) {
+                for (unsigned j = k >> 1; j > 0; j >>= 1) {
+                    for (unsigned p = tid; p < P / 2; p += kBucketThreads) {
+                        unsigned i, x;
+                        if (j == (k >> 1)) {   // the flip: i against its mirror in the k-block
+                            const unsigned blk = p / j, off = p % j;
+                            i = blk * k + off;
+                            x = blk * k + (k - 1 - off);
+                        } else {
+                            i = (p / j) * 2 * j + (p % j);
+                            x = i + j;
+                        }
+                        if (x < m && key_less<KW>(X + x * KW, X + i * KW)) {
+#pragma unroll
+                            for (int w = 0; w < KW; ++w) {
+                                const uint64_t t = X[i * KW + w];
+                                X[i * KW + w] = X[x * KW + w];
+                                X[x * KW + w] = t;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (unsigned i = tid; i < m * KW; i += kBucketThreads) data[(s0 + a0) * KW + i] = X[i];
+        }
+        for (unsigned i = tid; i < n; i += kBucketThreads) {
+            uint64_t k[KW];
+#pragma unroll
+            for (int w = 0; w < KW; ++w) k[w] = B[i * KW + w];
+            const unsigned bin = sub_of(k);
+            const unsigned a0 = st[bin], m = hist[bin];
+            if (m > kRankMax) continue;   // placed above
+            unsigned r = 0;
+            for (unsigned j = a0; j < a0 + m; ++j) r += key_less<KW>(B + j * KW, k) ? 1u : 0u;
+#pragma unroll
+            for (int w = 0; w < KW; ++w) data[(s0 + a0 + r) * KW + w] = k[w];
+        }
+        return;
+    }
     if (maxsub <= (unsigned)kRankMax) {
         // rank sort inside each sub-bin: a key's place is the number of keys
         // of its sub-bin below it (the keys are distinct); neighbouring

@@ -82,6 +82,9 @@ def test_more_than_2_to_the_28_distinct_keys():
     st = readsim.Stream(2828)
     gaps = (st.raw(n) >> np.uint64(31)) + np.uint64(1)           # 1 .. 2^33
     gaps[1000:1000 + (1 << 20)] = (gaps[1000:1000 + (1 << 20)] & np.uint64(15)) + np.uint64(1)
+    for c in range(40):   # clusters of 300..900 consecutive values: one shared-memory
+        at = (c + 1) * (n // 41)   # sub-bin of their segment holds them all
+        gaps[at:at + 300 + 15 * c] = 1
     want = np.cumsum(gaps, dtype=np.uint64)
     assert int(want[-1]) < (1 << 62) and len(want) > (1 << 28)
     stride = 1_000_003                                             # prime, coprime to n
@@ -113,6 +116,54 @@ def test_more_than_2_to_the_28_distinct_keys():
                                nhash, tau)
     assert np.array_equal(est[pick].astype(np.uint64), o_est), "estimates"
     assert (o_est == 0).any() and (o_est > tau).any()
+
+
+@pytest.mark.parametrize("K", [40, 55, 64])
+def test_two_word_top_bits_sort_with_clusters(K):
+    # 2^21 + 2^18 random two-word keys of K bases (past the size where two-word
+    # keys take the top-bits sort) with 60 planted clusters of 260..1,400 keys
+    # that differ only in their last bases, so that one shared-memory sub-bin
+    # of a segment holds a whole cluster; plus one run of 20,000 keys sharing
+    # their top 24 bits (a segment too large for shared memory)
+    bits = 2 * K
+    n = (1 << 21) + (1 << 18)
+    st = readsim.Stream(5500 + K)
+    hi = st.raw(n) & np.uint64((1 << (bits - 64)) - 1)
+    lo = st.raw(n)
+    for c in range(60):
+        at = c * (n // 61) + 7
+        m = 260 + 19 * c
+        hi[at:at + m] = hi[at]
+        lo[at:at + m] = (lo[at] & ~np.uint64(0xFFFFF)) | st.raw(m) & np.uint64(0xFFFFF)
+    run = slice(n - 30_000, n - 10_000)   # the same top 24 key bits
+    if bits - 64 >= 24:
+        hi[run] = (hi[run] & np.uint64((1 << (bits - 88)) - 1)) | np.uint64(0x5A5A5A << (bits - 88))
+    else:
+        below = 24 - (bits - 64)          # top bits that live in the low word
+        hi[run] = hi[n - 30_000]
+        lo[run] = (lo[run] & np.uint64((1 << (64 - below)) - 1)) | (lo[n - 30_000] >> np.uint64(64 - below) << np.uint64(64 - below))
+    keys = np.stack([lo, hi], axis=1)
+    order = np.lexsort((lo, hi))
+    want = keys[order]
+    keep = np.ones(n, bool)
+    keep[1:] = (want[1:, 0] != want[:-1, 0]) | (want[1:, 1] != want[:-1, 1])
+    want = want[keep]
+    m_cnt, alpha, nhash, tau = 1 << 24, 4, 4, 3
+    words = m_cnt // 16
+    cells = st.raw(words) & np.uint64(0x7777777777777777)
+    with kc.CountBF(K, m_cnt, alpha, nhash, tau) as bf:
+        kc.kmerco_set_counters(bf.h, cells, words)
+        kc.kmerco_add_distinct(bf.h, keys, n)
+        bf.classify()
+        got, est = bf.distinct()
+        trusted = bf.trusted()
+    assert len(want) > (1 << 21)
+    assert np.array_equal(got, want), "sorted distinct keys"
+    assert np.array_equal(trusted, want[est > tau])
+    pick = np.unique(st.integers(20_000, len(want)))
+    o_est, _ = oracle.classify(cells, want[pick, 1].copy(), want[pick, 0].copy(), K, m_cnt, alpha,
+                               nhash, tau)
+    assert np.array_equal(est[pick].astype(np.uint64), o_est)
 
 
 @pytest.mark.slow
