@@ -255,6 +255,29 @@ int kmerco_get_trusted(kmerco_t *h, uint64_t *keys, uint64_t cap, uint64_t *n);
 int kmerco_get_erroneous(kmerco_t *h, uint64_t *keys, uint64_t cap, uint64_t *n);
 
 /*
+ * Both classified lists of Algorithm 2 at once, without waiting: the copies
+ * of the trustworthy keys to `trusted` (n_trusted * key_words words) and of
+ * the erroneous keys to `erroneous` are queued on a result stream of the
+ * handle, after the classification, and the call returns.  Either pointer
+ * may be NULL (that list is not copied); each is host (pinned, for the copy
+ * to run asynchronously) or device memory owned by the caller, with room for
+ * tcap / ecap keys.  *nt and *ne receive the list lengths at once.
+ *
+ * The caller's buffers hold the lists after kmerco_sync(h); until then the
+ * caller must neither read nor free them.  Further insert and reset calls
+ * run beside the copies (they touch neither list); the next kmerco_classify
+ * of this handle waits on the device for them before it rewrites the lists,
+ * and on the host only when it must grow the lists' buffer.  Errors: ESTATE
+ * (not classified), ESIZE (a cap below its list; nothing queued), ECUDA.
+ */
+int kmerco_get_lists_async(kmerco_t *h, uint64_t *trusted, uint64_t tcap, uint64_t *erroneous,
+                           uint64_t ecap, uint64_t *nt, uint64_t *ne);
+
+/* Waits for all work of the handle: its stream, its host-input copies and
+ * its result copies.  Reports a device error flag if one was set. */
+int kmerco_sync(kmerco_t *h);
+
+/*
  * QcountBF-II (Algorithm 5) for n arbitrary packed keys: est[i] = 0 when any
  * of key i's k_h counters is zero, else their minimum.  keys and est are
  * host or device (layout as above).  Synchronises.

@@ -107,6 +107,9 @@ SIGNATURES = {
     "kmerco_get_distinct": (c_int, [c_void_p, c_void_p, c_void_p, c_uint64, _u64p]),
     "kmerco_get_trusted": (c_int, [c_void_p, c_void_p, c_uint64, _u64p]),
     "kmerco_get_erroneous": (c_int, [c_void_p, c_void_p, c_uint64, _u64p]),
+    "kmerco_get_lists_async": (c_int, [c_void_p, c_void_p, c_uint64, c_void_p, c_uint64, _u64p,
+                                       _u64p]),
+    "kmerco_sync": (c_int, [c_void_p]),
     "kmerco_query": (c_int, [c_void_p, c_void_p, c_uint64, c_void_p]),
     "kmerco_merge": (c_int, [c_void_p, c_void_p]),
     "kmerco_reset": (c_int, [c_void_p]),
@@ -278,6 +281,20 @@ def kmerco_get_erroneous(h: int, keys=None, cap: int = 0) -> int:
     n = c_uint64(0)
     _check(load().kmerco_get_erroneous(h, _ptr(keys), cap, byref(n)), "kmerco_get_erroneous")
     return n.value
+
+
+def kmerco_get_lists_async(h: int, trusted=None, tcap: int = 0, erroneous=None,
+                           ecap: int = 0) -> tuple[int, int]:
+    """Queues the copies of both classified lists and returns (n_trusted,
+    n_erroneous) at once; the buffers hold the lists after kmerco_sync(h)."""
+    nt, ne = c_uint64(0), c_uint64(0)
+    _check(load().kmerco_get_lists_async(h, _ptr(trusted), tcap, _ptr(erroneous), ecap,
+                                         byref(nt), byref(ne)), "kmerco_get_lists_async")
+    return nt.value, ne.value
+
+
+def kmerco_sync(h: int) -> None:
+    _check(load().kmerco_sync(h), "kmerco_sync")
 
 
 def kmerco_query(h: int, keys, n: int, est) -> None:

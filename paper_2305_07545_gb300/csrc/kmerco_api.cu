@@ -87,6 +87,9 @@ struct kmerco {
     uint64_t hist_partial_cap;
     unsigned long long *seg_scratch;      // classify of large key sets: segment bounds, big segments
     uint64_t seg_scratch_cap;
+    cudaStream_t out_stream;              // result copies of kmerco_get_lists_async
+    cudaEvent_t out_ready, out_done;      // lists written / copies finished
+    bool out_pending;                     // copies queued since the last classify
 };
 
 namespace {
@@ -153,6 +156,7 @@ void raw_free(const kmerco_t *h, void *p, uint64_t bytes) {
         // at once: the work that used it must have finished
         cudaStreamSynchronize(h->stream);
         if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+        if (h->out_stream) cudaStreamSynchronize(h->out_stream);
         h->free_fn(h->alloc_ctx, p, (size_t)bytes, (void *)h->stream);
         return;
     }
@@ -732,6 +736,7 @@ void kmerco_destroy(kmerco_t *h) {
     {
         DeviceGuard guard(h->device);
         if (h->stream) cudaStreamSynchronize(h->stream);
+        if (h->out_stream) cudaStreamSynchronize(h->out_stream);
         dev_free(h, h->G.cells, h->G.words * 8);
         dev_free(h, h->ctr, sizeof(DevCounters));
         dev_free(h, h->table, h->cap * h->kw * 8);
@@ -761,6 +766,9 @@ void kmerco_destroy(kmerco_t *h) {
             if (h->copy_ev[i]) cudaEventDestroy(h->copy_ev[i]);
         if (h->copy_fork) cudaEventDestroy(h->copy_fork);
         if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+        if (h->out_ready) cudaEventDestroy(h->out_ready);
+        if (h->out_done) cudaEventDestroy(h->out_done);
+        if (h->out_stream) cudaStreamDestroy(h->out_stream);
         if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
         cudaGetLastError();
     }
@@ -873,6 +881,24 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     return KMERCO_OK;
 }
 
+namespace {
+
+// Orders a classification that rewrites the lists (into `words` words) after
+// the result copies still queued: on the device when the lists' buffer is
+// kept, on the host when it must be reallocated under them.
+int wait_result_copies(kmerco_t *h, uint64_t words) {
+    if (!h->out_pending) return KMERCO_OK;
+    if (words > h->split_cap) {
+        KM_CUDA(cudaStreamSynchronize(h->out_stream));
+    } else {
+        KM_CUDA(cudaStreamWaitEvent(h->stream, h->out_done, 0));
+    }
+    h->out_pending = false;
+    return KMERCO_OK;
+}
+
+}  // namespace
+
 int kmerco_classify(kmerco_t *h) {
     Range range("kmerco_classify");
     if (!h) return KMERCO_EINVAL;
@@ -886,6 +912,7 @@ int kmerco_classify(kmerco_t *h) {
     KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, D * kw));
     KM_TRY(ensure(h, &h->alt1, &h->alt1_cap, D * kw));
     KM_TRY(ensure(h, &h->est, &h->est_cap, D));
+    KM_TRY(wait_result_copies(h, D * kw));
     KM_TRY(ensure(h, &h->split, &h->split_cap, D * kw));
     KM_TRY(ensure(h, &h->sort_scratch, &h->sort_scratch_cap, sort_scratch_words(D, kw)));
     KM_TRY(ensure(h, &h->split_scratch, &h->split_scratch_cap, split_scratch_words(D)));
@@ -1144,6 +1171,47 @@ int kmerco_get_erroneous(kmerco_t *h, uint64_t *keys, uint64_t cap, uint64_t *n)
     if (cap < E) return KMERCO_ESIZE;
     DeviceGuard guard(h->device);
     return copy_out(h, keys, h->split + h->n_trusted * h->kw, E * h->kw * 8);
+}
+
+int kmerco_get_lists_async(kmerco_t *h, uint64_t *trusted, uint64_t tcap, uint64_t *erroneous,
+                           uint64_t ecap, uint64_t *nt, uint64_t *ne) {
+    if (!h || !nt || !ne) return KMERCO_EINVAL;
+    if (!h->classified) return KMERCO_ESTATE;
+    const uint64_t T = h->n_trusted, E = h->n_distinct - h->n_trusted;
+    *nt = T;
+    *ne = E;
+    if ((trusted && tcap < T) || (erroneous && ecap < E)) return KMERCO_ESIZE;
+    if ((!trusted || T == 0) && (!erroneous || E == 0)) return KMERCO_OK;
+    DeviceGuard guard(h->device);
+    if (!h->out_stream) {
+        if (cudaStreamCreateWithFlags(&h->out_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->out_ready, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->out_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return KMERCO_ECUDA;
+        }
+    }
+    KM_CUDA(cudaEventRecord(h->out_ready, h->stream));
+    KM_CUDA(cudaStreamWaitEvent(h->out_stream, h->out_ready, 0));
+    const uint64_t w = (uint64_t)h->kw * 8;
+    if (trusted && T)
+        KM_CUDA(cudaMemcpyAsync(trusted, h->split, T * w, cudaMemcpyDefault, h->out_stream));
+    if (erroneous && E)
+        KM_CUDA(cudaMemcpyAsync(erroneous, h->split + T * h->kw, E * w, cudaMemcpyDefault,
+                                h->out_stream));
+    KM_CUDA(cudaEventRecord(h->out_done, h->out_stream));
+    h->out_pending = true;
+    return KMERCO_OK;
+}
+
+int kmerco_sync(kmerco_t *h) {
+    if (!h) return KMERCO_EINVAL;
+    DeviceGuard guard(h->device);
+    KM_CUDA(cudaStreamSynchronize(h->stream));
+    if (h->copy_stream) KM_CUDA(cudaStreamSynchronize(h->copy_stream));
+    if (h->out_stream) KM_CUDA(cudaStreamSynchronize(h->out_stream));
+    KM_TRY(read_counters(h));
+    return device_error_status(h->ctr_host->error);
 }
 
 int kmerco_query(kmerco_t *h, const uint64_t *keys, uint64_t n, uint32_t *est) {
@@ -1743,6 +1811,10 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
         KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, D[i] * kw));
         KM_TRY(ensure(h, &h->alt1, &h->alt1_cap, D[i] * kw));
         KM_TRY(ensure(h, &h->est, &h->est_cap, D[i]));
+        if (h->out_pending) {   // the batch writes the lists on its own streams
+            KM_CUDA(cudaStreamSynchronize(h->out_stream));
+            h->out_pending = false;
+        }
         KM_TRY(ensure(h, &h->split, &h->split_cap, D[i] * kw));
         KM_TRY(ensure(h, &h->sort_scratch, &h->sort_scratch_cap, sort_scratch_words(D[i], kw)));
         KM_TRY(ensure(h, &h->split_scratch, &h->split_scratch_cap, split_scratch_words(D[i])));
