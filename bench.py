@@ -47,7 +47,8 @@ L2_FLUSH_BYTES = 256 << 20
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "insert_phase_single.md")
 # per workload: the ncu summary holding the DRAM traffic record of its insert phase
 PROFILE_SUMMARIES = {"single": PROFILE_SUMMARY,
-                     "repeats": os.path.join(ROOT, "profiles", "insert_phase_repeats.md")}
+                     "repeats": os.path.join(ROOT, "profiles", "insert_phase_repeats.md"),
+                     "repeats55": os.path.join(ROOT, "profiles", "insert_phase_repeats.md")}
 SECONDARY = {"repeats": "repeats55"}   # workload timed after the headline one, same reads
 INSERT_SOURCES = [os.path.join(ROOT, "paper_2305_07545_gb300", "csrc", f)
                   for f in ("kmerco_insert.cu", "kmerco_internal.cuh")]
@@ -102,6 +103,8 @@ def recorded_traffic(workload: str = "single") -> float | None:
             for line in f:
                 if line.startswith("traffic_record"):
                     kv = dict(p.split("=", 1) for p in line.split()[1:])
+                    if kv.get("workload", workload) != workload:
+                        continue
                     if kv.get("source_sha") == source_sha():
                         return float(kv["dram_bytes_per_launch"])
     except Exception:
@@ -416,6 +419,8 @@ def time_workload(name: str, args, bases, offsets, d_bases, d_offsets, flush, cl
         dist.barrier()
     out = {"workload": w, "inserted": inserted, "distinct": distinct, "trusted": trusted,
            "total_ms": total_ms, "insert_ms": statistics.mean(insert_ms),
+           "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms),
+                       "max": max(step_ms)},
            "classify_ms": statistics.mean(classify_ms), "launches": launches,
            "clocks": clk.summary(), "e2e": None,
            "device_bytes": bf.stats()["device_bytes"]}
@@ -614,7 +619,8 @@ def run_ours(args) -> None:
             "unit": UNIT, "ms_per_step": r2["total_ms"] / args.steps,
             "kmers_per_step_per_gpu": r2["inserted"], "distinct_per_gpu": r2["distinct"],
             "trustworthy_per_gpu": r2["trusted"],
-            "phases": {"insert_ms": r2["insert_ms"], "classify_ms": r2["classify_ms"]},
+            "phases": {"insert_ms": r2["insert_ms"], "classify_ms": r2["classify_ms"],
+                       "step_ms": r2["step_ms"]},
             "roofline": workload_roofline(r2, sec_name, input_bytes, peak, peak_src, peaks,
                                           full_size),
             "gpu_launches": r2["launches"], "clocks": r2["clocks"],
@@ -647,7 +653,8 @@ def run_ours(args) -> None:
             "e2e": dict(r["e2e"], host_link=link) if r["e2e"] else None,
             "phases": {"insert_ms": r["insert_ms"], "classify_ms": r["classify_ms"],
                        "insert_kmers_per_s": r["inserted"] / (r["insert_ms"] / 1000.0),
-                       "classify_distinct_per_s": r["distinct"] / (r["classify_ms"] / 1000.0)},
+                       "classify_distinct_per_s": r["distinct"] / (r["classify_ms"] / 1000.0),
+                       "step_ms": r["step_ms"]},
             "secondary": secondary,
             "l2_atomic_peak": None if not peaks else {
                 "random_cas_per_s": {k: v["random_cas_per_s"] for k, v in peaks.items()},

@@ -36,18 +36,37 @@ def test_host_cpu_reports_model_and_cores():
 
 
 def test_traffic_records_are_well_formed():
-    # one record line per summary: the code hash it was taken on and the
-    # DRAM bytes of one call
+    # one record line per workload: the code hash it was taken on and the
+    # DRAM bytes of one call (a summary covering several workloads names
+    # each record's workload)
     import os
-    for path in bench.PROFILE_SUMMARIES.values():
+    for wl, path in bench.PROFILE_SUMMARIES.items():
         if not os.path.exists(path):
             continue
-        lines = [l for l in open(path) if l.startswith("traffic_record")]
-        assert len(lines) == 1
-        kv = dict(p.split("=", 1) for p in lines[0].split()[1:])
+        recs = []
+        for line in open(path):
+            if line.startswith("traffic_record"):
+                kv = dict(p.split("=", 1) for p in line.split()[1:])
+                if kv.get("workload", wl) == wl:
+                    recs.append(kv)
+        assert len(recs) == 1, wl
+        kv = recs[0]
         assert len(kv["source_sha"]) == 16 and int(kv["source_sha"], 16) >= 0
         assert float(kv["dram_bytes_per_launch"]) > 0
     assert len(bench.source_sha()) == 16
+
+
+def test_recorded_traffic_matches_by_workload(tmp_path, monkeypatch):
+    f = tmp_path / "p.md"
+    sha = bench.source_sha()
+    f.write_text(f"traffic_record workload=a source_sha={sha} dram_bytes_per_launch=100\n"
+                 f"traffic_record workload=b source_sha={sha} dram_bytes_per_launch=200\n"
+                 f"traffic_record workload=c source_sha=0000000000000000 dram_bytes_per_launch=1\n")
+    monkeypatch.setattr(bench, "PROFILE_SUMMARIES", {"a": str(f), "b": str(f), "c": str(f)})
+    assert bench.recorded_traffic("a") == 100.0
+    assert bench.recorded_traffic("b") == 200.0
+    assert bench.recorded_traffic("c") is None      # taken on other code
+    assert bench.recorded_traffic("d") is None      # no summary
 
 
 def test_batch_groups_respect_the_memory_limit():
