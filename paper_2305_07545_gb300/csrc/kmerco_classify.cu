@@ -643,19 +643,39 @@ __global__ void seg_bounds_kernel(const uint64_t *keys, uint64_t n, int bits, ui
 
 // Segment j = [b[j], b[j + 1]) of `data` sorted in place by one block.
 // Segments above seg_cap<KW>() keys go to the `big` list (begin, count)
-// instead; nbig counts them.
+// instead; nbig counts them.  The keys are loaded before anything else: the
+// segment's top-bit range comes from its first and last key as loaded.
+// Each key's sub-bin is computed once and kept beside it in shared memory.
+template <int KW>
+__device__ __forceinline__ unsigned rank_in_subbin(const uint64_t *B, unsigned a0, unsigned m,
+                                                   const uint64_t *k) {
+    unsigned r = 0;
+    if (KW == 1) {
+        for (unsigned j = a0; j < a0 + m; ++j) r += B[j] < k[0] ? 1u : 0u;
+    } else {   // one 16-byte shared load per key: x the low word, y the high word
+        const ulonglong2 *B2 = (const ulonglong2 *)B;
+        for (unsigned j = a0; j < a0 + m; ++j) {
+            const ulonglong2 v = B2[j];
+            r += (v.y < k[1] || (v.y == k[1] && v.x < k[0])) ? 1u : 0u;
+        }
+    }
+    return r;
+}
+
 template <int KW>
 __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
     uint64_t *data, int bits, const unsigned long long *b, unsigned long long *big,
     unsigned long long *nbig) {
     constexpr int C = seg_cap<KW>();
     constexpr unsigned kPer = C / kBucketThreads;
-    extern __shared__ unsigned long long sm[];
-    uint64_t *B = (uint64_t *)sm;            // C keys of KW words
-    unsigned *hist = (unsigned *)(sm + C * KW);
-    unsigned *st = hist + kSubBins, *fill = st + kSubBins;
+    extern __shared__ __align__(16) unsigned long long sm[];
+    uint64_t *B = (uint64_t *)sm;                  // C keys of KW words
+    unsigned *cnt = (unsigned *)(sm + C * KW);     // per sub-bin: count, then fill cursor
+    unsigned *st = cnt + kSubBins;                 // per sub-bin: first place
+    uint16_t *SB = (uint16_t *)(st + kSubBins);    // sub-bin of the key at B[i]
     __shared__ unsigned maxsub, nlarge;
     __shared__ unsigned large[kMaxLarge];   // sub-bins above kRankMax keys
+    __shared__ uint32_t tops[2];            // top bits of the first and the last key
     const uint64_t s0 = b[blockIdx.x], e0 = b[blockIdx.x + 1];
     if (e0 <= s0 + 1) return;   // empty or one key
     const uint64_t nn = e0 - s0;
@@ -669,41 +689,46 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
     }
     const unsigned n = (unsigned)nn;
     const unsigned tid = threadIdx.x;
-    // the segment's top-bit range [t0, t1] maps onto kSubBins sub-bins of
-    // the key's top min(bits, 64) bits
-    const int pb = bits < 64 ? bits : 64;
-    const uint32_t t0 = top_bits<KW>(data + s0 * KW, bits);
-    const uint32_t t1 = top_bits<KW>(data + (e0 - 1) * KW, bits);
-    const int below = pb - kTopBits;                      // prefix bits under the top bits
-    int span = 0;
-    while ((1ull << span) < (uint64_t)(t1 - t0 + 1)) ++span;
-    int r = span + below - 12;
-    if (r < 0) r = 0;
-    const uint64_t base = (uint64_t)t0 << below;
-    for (unsigned i = tid; i < kSubBins; i += kBucketThreads) hist[i] = 0;
-    if (tid == 0) {
-        maxsub = 0;
-        nlarge = 0;
-    }
-    __syncthreads();
-    // sub-bin of a key (recomputed where needed: registers hold the keys)
-    auto sub_of = [&](const uint64_t *k) {
-        return (unsigned)min((bits_from<KW>(k, bits - pb) - base) >> r, (uint64_t)kSubBins - 1);
-    };
     uint64_t key[kPer][KW];
 #pragma unroll
     for (unsigned q = 0; q < kPer; ++q) {
         const unsigned i = q * kBucketThreads + tid;
 #pragma unroll
         for (int w = 0; w < KW; ++w) key[q][w] = i < n ? data[(s0 + i) * KW + w] : 0ull;
-        if (i < n) atomicAdd(&hist[sub_of(key[q])], 1u);
     }
+    for (unsigned i = tid; i < kSubBins; i += kBucketThreads) cnt[i] = 0;
+    if (tid == 0) {
+        maxsub = 0;
+        nlarge = 0;
+        tops[0] = top_bits<KW>(key[0], bits);
+    }
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q)
+        if (q * kBucketThreads + tid == n - 1) tops[1] = top_bits<KW>(key[q], bits);
+    __syncthreads();
+    // the segment's top-bit range [t0, t1] maps onto kSubBins sub-bins of
+    // the key's top min(bits, 64) bits
+    const int pb = bits < 64 ? bits : 64;
+    const uint32_t t0 = tops[0], t1 = tops[1];
+    const int below = pb - kTopBits;                      // prefix bits under the top bits
+    int span = 0;
+    while ((1ull << span) < (uint64_t)(t1 - t0 + 1)) ++span;
+    int r = span + below - 12;
+    if (r < 0) r = 0;
+    const uint64_t base = (uint64_t)t0 << below;
+    // sub-bin of a key (computed again for the scatter: registers hold the keys)
+    auto sub_of = [&](const uint64_t *k) {
+        return (unsigned)min((bits_from<KW>(k, bits - pb) - base) >> r, (uint64_t)kSubBins - 1);
+    };
+#pragma unroll
+    for (unsigned q = 0; q < kPer; ++q)
+        if (q * kBucketThreads + tid < n) atomicAdd(&cnt[sub_of(key[q])], 1u);
     __syncthreads();
     {
         unsigned v[4], sum = 0, mx = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            v[j] = hist[tid * 4 + j];
+            v[j] = cnt[tid * 4 + j];
             sum += v[j];
             mx = max(mx, v[j]);
         }
@@ -712,7 +737,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             st[tid * 4 + j] = pre;
-            fill[tid * 4 + j] = pre;
+            cnt[tid * 4 + j] = pre;   // fill cursor; after the scatter, the sub-bin's end
             pre += v[j];
             if (v[j] > kRankMax) {
                 const unsigned q = atomicAdd(&nlarge, 1u);
@@ -725,9 +750,11 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
 #pragma unroll
     for (unsigned q = 0; q < kPer; ++q) {
         if (q * kBucketThreads + tid < n) {
-            const unsigned at = atomicAdd(&fill[sub_of(key[q])], 1u);
+            const unsigned bin = sub_of(key[q]);
+            const unsigned at = atomicAdd(&cnt[bin], 1u);
 #pragma unroll
             for (int w = 0; w < KW; ++w) B[at * KW + w] = key[q][w];
+            SB[at] = (uint16_t)bin;
         }
     }
     __syncthreads();
@@ -737,7 +764,7 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
         // the smaller key first; a partner past the end stands for +infinity
         // and is skipped), the others rank sorted as below
         for (unsigned q = 0; q < nlarge; ++q) {
-            const unsigned a0 = st[large[q]], m = hist[large[q]];
+            const unsigned a0 = st[large[q]], m = cnt[large[q]] - a0;
             uint64_t *X = B + (uint64_t)a0 * KW;
             unsigned P = 2;
             while (P < m) P <<= 1;
@@ -767,65 +794,53 @@ __global__ void __launch_bounds__(kBucketThreads, 2) segment_sort_kernel(
             }
             for (unsigned i = tid; i < m * KW; i += kBucketThreads) data[(s0 + a0) * KW + i] = X[i];
         }
-        for (unsigned i = tid; i < n; i += kBucketThreads) {
-            uint64_t k[KW];
-#pragma unroll
-            for (int w = 0; w < KW; ++w) k[w] = B[i * KW + w];
-            const unsigned bin = sub_of(k);
-            const unsigned a0 = st[bin], m = hist[bin];
-            if (m > kRankMax) continue;   // placed above
-            unsigned r = 0;
-            for (unsigned j = a0; j < a0 + m; ++j) r += key_less<KW>(B + j * KW, k) ? 1u : 0u;
-#pragma unroll
-            for (int w = 0; w < KW; ++w) data[(s0 + a0 + r) * KW + w] = k[w];
-        }
-        return;
     }
-    if (maxsub <= (unsigned)kRankMax) {
+    if (maxsub <= (unsigned)kRankMax || nlarge <= kMaxLarge) {
         // rank sort inside each sub-bin: a key's place is the number of keys
         // of its sub-bin below it (the keys are distinct); neighbouring
         // threads mostly share a sub-bin, so the loop reads are broadcasts.
-        // Each key goes straight to its place in global memory.
+        // Each key goes straight to its place in global memory.  Sub-bins
+        // above kRankMax keys were placed above.
         for (unsigned i = tid; i < n; i += kBucketThreads) {
             uint64_t k[KW];
 #pragma unroll
             for (int w = 0; w < KW; ++w) k[w] = B[i * KW + w];
-            const unsigned bin = sub_of(k);
-            const unsigned a0 = st[bin], m = hist[bin];
-            unsigned r = 0;
-            for (unsigned j = a0; j < a0 + m; ++j) r += key_less<KW>(B + j * KW, k) ? 1u : 0u;
+            const unsigned bin = SB[i];
+            const unsigned a0 = st[bin], m = cnt[bin] - a0;
+            if (m > kRankMax) continue;
+            const unsigned rk = rank_in_subbin<KW>(B, a0, m, k);
 #pragma unroll
-            for (int w = 0; w < KW; ++w) data[(s0 + a0 + r) * KW + w] = k[w];
+            for (int w = 0; w < KW; ++w) data[(s0 + a0 + rk) * KW + w] = k[w];
         }
         return;
-    } else {   // clustered keys: bitonic sort of the whole segment (all-ones pads sort last)
-        unsigned P = 2;
-        while (P < n) P <<= 1;
-        for (unsigned i = n + tid; i < P; i += kBucketThreads)
+    }
+    // many clustered sub-bins: bitonic sort of the whole segment (all-ones
+    // pads sort last)
+    unsigned P = 2;
+    while (P < n) P <<= 1;
+    for (unsigned i = n + tid; i < P; i += kBucketThreads)
 #pragma unroll
-            for (int w = 0; w < KW; ++w) B[i * KW + w] = ~0ull;
-        __syncthreads();
-        for (unsigned k = 2; k <= P; k <<= 1) {
-            for (unsigned j = k >> 1; j > 0; j >>= 1) {
-                for (unsigned i = tid; i < P; i += kBucketThreads) {
-                    const unsigned ixj = i ^ j;
-                    if (ixj > i) {
-                        const bool up = (i & k) == 0;
-                        if (key_less<KW>(B + ixj * KW, B + i * KW) == up) {
+        for (int w = 0; w < KW; ++w) B[i * KW + w] = ~0ull;
+    __syncthreads();
+    for (unsigned k = 2; k <= P; k <<= 1) {
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            for (unsigned i = tid; i < P; i += kBucketThreads) {
+                const unsigned ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    if (key_less<KW>(B + ixj * KW, B + i * KW) == up) {
 #pragma unroll
-                            for (int w = 0; w < KW; ++w) {
-                                const uint64_t t = B[i * KW + w];
-                                B[i * KW + w] = B[ixj * KW + w];
-                                B[ixj * KW + w] = t;
-                            }
+                        for (int w = 0; w < KW; ++w) {
+                            const uint64_t t = B[i * KW + w];
+                            B[i * KW + w] = B[ixj * KW + w];
+                            B[ixj * KW + w] = t;
                         }
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
         }
     }
-    __syncthreads();
     for (unsigned i = tid; i < n * KW; i += kBucketThreads) data[s0 * KW + i] = B[i];
 }
 
@@ -1031,8 +1046,9 @@ cudaError_t top_segment_sort(uint64_t *data, uint64_t n, int kw, int bits, unsig
         seg_bounds_kernel<1><<<g, 256, 0, s>>>(data, n, bits, H, nb, b);
     else
         seg_bounds_kernel<2><<<g, 256, 0, s>>>(data, n, bits, H, nb, b);
-    const int smem1 = seg_cap<1>() * 8 + 3 * kSubBins * 4;
-    const int smem2 = seg_cap<2>() * 16 + 3 * kSubBins * 4;
+    // keys, two arrays per sub-bin, one 16-bit sub-bin per key
+    const int smem1 = seg_cap<1>() * (8 + 2) + 2 * kSubBins * 4;
+    const int smem2 = seg_cap<2>() * (16 + 2) + 2 * kSubBins * 4;
     if (kw == 1) {
         e = cudaFuncSetAttribute(segment_sort_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem1);
