@@ -40,7 +40,8 @@ struct kmerco {
     void *alloc_ctx;
     Geometry G;
     DevCounters *ctr;        // device
-    DevCounters *ctr_host;   // pinned mirror
+    DevCounters *ctr_host;   // pinned, mapped mirror
+    DevCounters *ctr_mirror; // the mirror's device address
     uint64_t *table;         // distinct-key set: cap slots of kw words
     uint64_t cap;
     uint32_t gen;            // generation tag of the set's current keys
@@ -203,9 +204,22 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The counters are written into the mapped pinned mirror by a kernel, not
+// copied by a copy engine: a device-to-host copy would queue behind any
+// large copy in flight in that direction (the lists of the previous sample
+// that kmerco_get_lists_async is still moving), and every readback of the
+// next insert would wait for it.
+__global__ void mirror_counters_kernel(const unsigned long long *src, unsigned long long *dst) {
+    const unsigned i = threadIdx.x;
+    if (i < sizeof(DevCounters) / 8) dst[i] = src[i];
+}
+static_assert(sizeof(DevCounters) % 8 == 0, "the mirror is copied in 8-byte words");
+
 int read_counters(kmerco_t *h) {
-    KM_CUDA(cudaMemcpyAsync(h->ctr_host, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
-                            h->stream));
+    mirror_counters_kernel<<<1, 32, 0, h->stream>>>((const unsigned long long *)h->ctr,
+                                                    (unsigned long long *)h->ctr_mirror);
+    KM_CUDA(cudaGetLastError());
+    h->launches += 1;
     KM_CUDA(cudaStreamSynchronize(h->stream));
     return KMERCO_OK;
 }
@@ -710,8 +724,16 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
         G.cells = (uint64_t *)p;
         if ((status = dev_alloc(h, &p, sizeof(DevCounters)))) break;
         h->ctr = (DevCounters *)p;
-        if (cudaMallocHost((void **)&h->ctr_host, sizeof(DevCounters)) != cudaSuccess) {
+        if (cudaHostAlloc((void **)&h->ctr_host, sizeof(DevCounters), cudaHostAllocMapped) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            h->ctr_host = nullptr;
             status = KMERCO_ENOMEM;
+            break;
+        }
+        if (cudaHostGetDevicePointer((void **)&h->ctr_mirror, h->ctr_host, 0) != cudaSuccess) {
+            cudaGetLastError();
+            status = KMERCO_ECUDA;
             break;
         }
         memset(h->ctr_host, 0, sizeof(DevCounters));
@@ -811,17 +833,20 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
     HostCopy hc;
     bool copying = false;
     if (host_offsets) {   // checked and summed on the device too
+        // the offsets go first: a check that waits for them then does not wait
+        // for the reads' bytes queued behind them on the copy engine
+        KM_TRY(ensure(h, &h->in_offsets, &h->in_offsets_cap, nreads + 1));
+        KM_CUDA(cudaMemcpyAsync(h->in_offsets, offsets, (nreads + 1) * 8, cudaMemcpyHostToDevice,
+                                h->stream));
+        d_off = h->in_offsets;
         if (host_bases && offsets[nreads] > offsets[0]) {
-            // the reads' bytes start moving now, while the offsets are checked
+            // the reads' bytes start moving now, while the offsets are checked;
+            // the insert launches wait only for the pieces they read
             const uint64_t nb = offsets[nreads] - offsets[0];
             KM_TRY(ensure(h, &h->in_bases, &h->in_bases_cap, nb));
             KM_TRY(issue_host_copy(h, (const uint8_t *)bases + offsets[0], h->in_bases, nb, hc));
             copying = true;
         }
-        KM_TRY(ensure(h, &h->in_offsets, &h->in_offsets_cap, nreads + 1));
-        KM_CUDA(cudaMemcpyAsync(h->in_offsets, offsets, (nreads + 1) * 8, cudaMemcpyHostToDevice,
-                                h->stream));
-        d_off = h->in_offsets;
     }
     if (host_offsets && nreads <= kHostBoundReads) {
         // summed on the host: the call does not wait for the device
