@@ -326,6 +326,20 @@ def max_over_ranks(x: float, device) -> float:
     return float(t.item())
 
 
+def l2_note(countbf_bytes: int, input_bytes: int, l2_bytes: int) -> str:
+    """How the timed steps stand to an L2 of l2_bytes: what the flush between
+    them does and which of the step's data can stay resident."""
+    flush = (f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps, outside the "
+             f"per-step CUDA events; L2 {l2_bytes / 2**20:.0f} MiB (device properties)")
+    if countbf_bytes * 2 <= l2_bytes:
+        return (f"{flush}; the {countbf_bytes / 2**20:.1f} MiB countBF is L2-resident within a "
+                "step by design (the L2-atomic regime); the flush evicts it between steps")
+    if countbf_bytes <= 2 * l2_bytes:
+        return (f"{flush}; the {countbf_bytes / 2**20:.0f} MiB countBF is about the size of "
+                f"L2, the {input_bytes / 1e9:.2f} GB of inputs larger")
+    return f"{flush}; inputs ({input_bytes / 1e9:.2f} GB) and countBF larger than L2"
+
+
 def whole_job_rate(units_per_rank_step: int, steps: int, world: int, slowest_s: float) -> float:
     """Units all ranks processed divided by the slowest rank's time (weak scaling:
     every rank processes its own sample of the same size)."""
@@ -646,8 +660,9 @@ def run_ours(args) -> None:
                        "kmers_per_step_per_gpu": r["inserted"], "distinct_per_gpu": r["distinct"],
                        "trustworthy_per_gpu": r["trusted"],
                        "parallelism": f"{world} independent samples, one per GPU",
-                       "l2": "256 MiB buffer written between timed steps, outside the "
-                             "per-step CUDA events; inputs and countBF larger than L2",
+                       "l2": l2_note(w.m * w.alpha // 8, input_bytes,
+                                     getattr(torch.cuda.get_device_properties(dev),
+                                             "L2_cache_size", 126 << 20)),
                        "device_bytes": r["device_bytes"],
                        "read_generation_s": round(t_gen, 1)},
             "roofline": roofline, "cpu_baseline": cpu,

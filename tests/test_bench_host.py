@@ -76,3 +76,10 @@ def test_batch_groups_respect_the_memory_limit():
     for g in groups:
         assert len(g) == 1 or sum(sizes[i] for i in g) <= 10
     assert bench.batch_groups(sizes, 1000) == [list(range(len(sizes)))]
+
+
+def test_l2_note_names_the_regime():
+    l2 = 126 << 20
+    assert "L2-resident" in bench.l2_note(512 << 10, 200_000, l2)          # tiny: 512 KiB
+    assert "about the size of L2" in bench.l2_note(128 << 20, 150e6, l2)   # single: 128 MiB
+    assert "larger than L2" in bench.l2_note(4 << 30, 3.16e9, l2)          # repeats: 4 GiB
