@@ -156,3 +156,18 @@ def test_torch_allocator_with_a_batch():
                 assert np.array_equal(f.distinct()[0], ref.distinct_lo)
     for f in filters:
         f.close()
+
+
+
+def test_pass_size_bounds():
+    # at most 2^31 increments per partitioned pass
+    with pytest.raises(kc.KmercoError) as e:
+        kc.CountBF(21, 1 << 20, 4, 3, 2, update_mode=kc.UPDATE_PARTITIONED,
+                   pass_codes=(1 << 31) + 1)
+    assert e.value.status == kc.EINVAL
+    b, o = readsim.scaled("tiny", 800, seed_offset=123).generate()
+    for alpha in (4, 16):   # counting and compare-and-swap apply, one full-size pass
+        with kc.CountBF(21, 1 << 22, alpha, 3, 2, update_mode=kc.UPDATE_PARTITIONED,
+                        pass_codes=1 << 31) as bf:
+            bf.insert(_dev(b), _dev(o))
+            _exact(bf, b, o, 21, 1 << 22, alpha, 3, 2)
