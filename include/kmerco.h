@@ -221,7 +221,10 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
  * distinct-key set ascending, estimate each key as 0 if any of its k_h
  * counters is 0 and otherwise their minimum, and split the keys into
  * trustworthy (estimate > tau) and erroneous (estimate <= tau), both kept in
- * ascending order.  Synchronises.  Idempotent until the next insert.
+ * ascending order.  The split needs only whether the estimate exceeds tau,
+ * so a key's counters are read until one is at or below tau; the full
+ * estimates of erroneous keys are computed when kmerco_get_distinct() asks
+ * for them.  Synchronises.  Idempotent until the next insert.
  * Errors: ETIMEOUT if an earlier insert's bounded retry loop gave up;
  * EINVAL if an earlier insert found decreasing offsets; ENOMEM; ECUDA.
  */
@@ -241,7 +244,8 @@ int kmerco_get_counters(kmerco_t *h, uint64_t *dst, uint64_t nwords);
 /*
  * Copy the distinct keys (ascending) and their estimates after
  * kmerco_classify().  keys: host or device, room for cap keys (cap * words
- * per key uint64_t); est: host or device, cap uint32_t, or NULL.  *n
+ * per key uint64_t); est: host or device, cap uint32_t, or NULL (the first
+ * call with est computes every key's estimate, one query pass).  *n
  * receives the number of distinct keys; keys == NULL only queries it.
  * ESTATE before classify (or after a later insert), ESIZE when cap < *n.
  */

@@ -70,6 +70,8 @@ struct kmerco {
     const uint64_t *sorted;  // sorted distinct keys (one of dlist, alt0, alt1)
     uint64_t n_distinct, n_trusted;
     bool classified;
+    bool est_exact;          // est holds Algorithm 5's value for every key, not only
+                             // for the trustworthy ones
     cudaEvent_t ev[4];
     cudaStream_t copy_stream;                      // host input copies (created on first use)
     cudaEvent_t copy_ev[kCopyPieces + 1], copy_fork;
@@ -1071,7 +1073,8 @@ int kmerco_classify(kmerco_t *h) {
         if (D > 1) h->launches += 3 * (uint64_t)passes;
     }
 sorted_done:
-    KM_CUDA(launch_query(sorted, D, kw, h->K, h->G, h->est, h->stream));
+    KM_CUDA(launch_classify_query(sorted, D, kw, h->G, h->tau, h->est, h->stream));
+    h->est_exact = false;
     KM_CUDA(launch_split(sorted, h->est, D, kw, h->tau, h->split, h->split_scratch, h->ctr,
                          h->stream));
     if (D > 0) h->launches += 4;   // query + three split kernels
@@ -1173,7 +1176,14 @@ int kmerco_get_distinct(kmerco_t *h, uint64_t *keys, uint32_t *est, uint64_t cap
     if (cap < h->n_distinct) return KMERCO_ESIZE;
     DeviceGuard guard(h->device);
     KM_TRY(copy_out(h, keys, h->sorted, h->n_distinct * h->kw * 8));
-    if (est) KM_TRY(copy_out(h, est, h->est, h->n_distinct * 4));
+    if (est) {
+        if (!h->est_exact) {   // the estimates of erroneous keys in full (Algorithm 5)
+            KM_CUDA(launch_query(h->sorted, h->n_distinct, h->kw, h->K, h->G, h->est, h->stream));
+            h->launches += h->n_distinct ? 1 : 0;
+            h->est_exact = true;
+        }
+        KM_TRY(copy_out(h, est, h->est, h->n_distinct * 4));
+    }
     return KMERCO_OK;
 }
 
@@ -1906,7 +1916,7 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
                 const uint64_t *sorted = h->dlist;
                 KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D[i], h->kw, bits,
                                    h->sort_scratch, &sorted, st));
-                KM_CUDA(launch_query(sorted, D[i], h->kw, h->K, h->G, h->est, st));
+                KM_CUDA(launch_classify_query(sorted, D[i], h->kw, h->G, h->tau, h->est, st));
                 KM_CUDA(launch_split(sorted, h->est, D[i], h->kw, h->tau, h->split,
                                      h->split_scratch, h->ctr, st));
                 const uint64_t n_launch = (D[i] > 1 ? 3 * (uint64_t)passes : 0) + (D[i] ? 4 : 0);
@@ -1953,6 +1963,7 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
         if (h->classified) continue;
         h->n_trusted = h->ctr_host->trusted;
         h->classified = true;
+        h->est_exact = false;
         h->classify_timed = false;
     }
     return KMERCO_OK;

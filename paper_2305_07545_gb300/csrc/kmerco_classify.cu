@@ -247,6 +247,48 @@ __global__ void query_kernel(const uint64_t *keys, uint64_t n, int K, Geometry G
     }
 }
 
+// Algorithm 5 as far as Algorithm 2 needs it.  The split asks only whether
+// est > tau, and est is the minimum of the key's k_h counters, so the first
+// counter at or below tau decides "erroneous": the remaining counters of that
+// key are not read.  est[i] is then exact for every trustworthy key (all k_h
+// counters read) and, for an erroneous key, the minimum of the counters read
+// so far, which is at most tau; Algorithm 5's 0 for an empty counter is that
+// minimum too.  Each lane works through its keys one counter per iteration
+// (a finished key makes room for the lane's next key at once), so every
+// iteration keeps one random counter read per lane in flight.
+template <int KW>
+__global__ void __launch_bounds__(256) classify_query_kernel(const uint64_t *keys, uint64_t n,
+                                                             Geometry G, uint32_t tau,
+                                                             uint32_t *est) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t klo = keys[i * KW], khi = KW == 2 ? keys[i * KW + 1] : 0;
+    uint64_t k1m = KW == 1 ? premix8(klo) : 0;
+    unsigned j = 0;
+    uint64_t best = ~0ull;
+    for (;;) {
+        uint64_t h1, h2, cell;
+        unsigned slot;
+        if (KW == 1)
+            murmur8(k1m, j, h1, h2);
+        else
+            murmur16(klo, khi, j, h1, h2);
+        address(G, h1, cell, slot);
+        const uint64_t v = (__ldg(G.cells + cell) >> (slot * (unsigned)G.alpha)) & G.maxc;
+        best = v < best ? v : best;
+        if (++j < (unsigned)G.nhash && best > tau) continue;
+        est[i] = (uint32_t)best;
+        i += stride;
+        if (i >= n) break;
+        klo = keys[i * KW];
+        khi = KW == 2 ? keys[i * KW + 1] : 0;
+        k1m = KW == 1 ? premix8(klo) : 0;
+        j = 0;
+        best = ~0ull;
+    }
+}
+
 // Trusted keys per split tile.  A tile of kSplitTile keys is read in 16
 // rounds of kSortThreads consecutive keys (coalesced), key tile0 + 256j + tid.
 __global__ void __launch_bounds__(kSortThreads) split_count_kernel(const uint32_t *est, uint64_t n,
@@ -1117,6 +1159,17 @@ cudaError_t launch_query(const uint64_t *keys, uint64_t n, int kw, int K, Geomet
         query_kernel<1><<<g, 256, 0, s>>>(keys, n, K, G, est);
     else
         query_kernel<2><<<g, 256, 0, s>>>(keys, n, K, G, est);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_query(const uint64_t *keys, uint64_t n, int kw, Geometry G,
+                                  uint32_t tau, uint32_t *est, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned g = grid_for(n, 256, 152 * 8);
+    if (kw == 1)
+        classify_query_kernel<1><<<g, 256, 0, s>>>(keys, n, G, tau, est);
+    else
+        classify_query_kernel<2><<<g, 256, 0, s>>>(keys, n, G, tau, est);
     return cudaGetLastError();
 }
 

@@ -419,6 +419,10 @@ cudaError_t bucket_place_and_sort(const uint64_t *in, uint64_t *out, uint64_t n,
 
 cudaError_t launch_query(const uint64_t *keys, uint64_t n, int kw, int K, Geometry G,
                          uint32_t *est, cudaStream_t s);
+// Algorithm 5 only as far as the split on tau needs it (classify_query_kernel):
+// est exact for keys above tau, at most tau otherwise.
+cudaError_t launch_classify_query(const uint64_t *keys, uint64_t n, int kw, Geometry G,
+                                  uint32_t tau, uint32_t *est, cudaStream_t s);
 // est > tau split, stable: trusted keys to out[0, T), erroneous to out[T, n);
 // T written to ctr->trusted.  scratch needs split_scratch_words(n) uint64.
 uint64_t split_scratch_words(uint64_t n);
