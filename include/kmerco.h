@@ -235,6 +235,19 @@ int kmerco_classify(kmerco_t *h);
 int kmerco_stats(kmerco_t *h, kmerco_stats_t *s);
 
 /*
+ * A 128-bit digest of the countBF cells, computed on the device, so that two
+ * countBFs can be compared without copying them out (the serving loop checks
+ * that a job's countBF is the same alone and among other jobs).  With
+ * f(x) = the MurmurHash3 64-bit finalizer and C = 0x9E3779B97F4A7C15:
+ *   out[0] = sum over cells i of f(cell[i] ^ (i * C))            mod 2^64
+ *   out[1] = sum over cells i of f(cell[i] + f(i + 1))           mod 2^64
+ * Not cryptographic: equal countBFs give equal digests; different ones
+ * collide only by chance.  out: host pointer to two uint64_t.
+ * Synchronises.  Errors: EINVAL (NULL), ECUDA.
+ */
+int kmerco_digest(kmerco_t *h, uint64_t *out);
+
+/*
  * Copy the countBF cells (Section 2.1 layout: counter l of a cell in bits
  * [alpha*l, alpha*l + alpha), wasted high bits zero) to dst (host or
  * device).  nwords must be >= stats.words; fewer gives ESIZE.

@@ -110,6 +110,7 @@ SIGNATURES = {
     "kmerco_get_lists_async": (c_int, [c_void_p, c_void_p, c_uint64, c_void_p, c_uint64, _u64p,
                                        _u64p]),
     "kmerco_sync": (c_int, [c_void_p]),
+    "kmerco_digest": (c_int, [c_void_p, c_void_p]),
     "kmerco_query": (c_int, [c_void_p, c_void_p, c_uint64, c_void_p]),
     "kmerco_merge": (c_int, [c_void_p, c_void_p]),
     "kmerco_reset": (c_int, [c_void_p]),
@@ -295,6 +296,13 @@ def kmerco_get_lists_async(h: int, trusted=None, tcap: int = 0, erroneous=None,
 
 def kmerco_sync(h: int) -> None:
     _check(load().kmerco_sync(h), "kmerco_sync")
+
+
+def kmerco_digest(h: int) -> tuple[int, int]:
+    """The countBF's 128-bit device-side digest (two 64-bit sums)."""
+    out = np.zeros(2, np.uint64)
+    _check(load().kmerco_digest(h, _ptr(out)), "kmerco_digest")
+    return int(out[0]), int(out[1])
 
 
 def kmerco_query(h: int, keys, n: int, est) -> None:
@@ -507,6 +515,11 @@ class CountBF:
         keys = np.zeros(self._shape(max(n, 1)), np.uint64)
         kmerco_get_erroneous(self.h, keys, n)
         return keys[:n]
+
+    def digest(self) -> str:
+        """Hex digest of the countBF cells, computed on the device."""
+        d0, d1 = kmerco_digest(self.h)
+        return f"{d0:016x}{d1:016x}"
 
     def query(self, keys: np.ndarray) -> np.ndarray:
         keys = np.ascontiguousarray(keys, np.uint64)

@@ -23,6 +23,10 @@ constexpr int kCopyPieces = 8;   // pieces of a host input copied while earlier 
 // larger ones are copied and summed by a kernel, which the call waits for.
 constexpr uint64_t kHostBoundReads = 1ull << 22;
 
+// The handle's device counters and their pinned mirror hold a DevCounters
+// followed by kmerco_digest's two sums.
+constexpr size_t kCtrBytes = sizeof(DevCounters) + 2 * sizeof(unsigned long long);
+
 struct kmerco {
     int K, kw, alpha, eta, nhash, canonical;   // canonical: 0 forward, 1 lexicographic, 2 hash
     int whole_file;
@@ -213,9 +217,34 @@ bool is_device_ptr(const void *p) {
 // next insert would wait for it.
 __global__ void mirror_counters_kernel(const unsigned long long *src, unsigned long long *dst) {
     const unsigned i = threadIdx.x;
-    if (i < sizeof(DevCounters) / 8) dst[i] = src[i];
+    if (i < kCtrBytes / 8) dst[i] = src[i];
 }
 static_assert(sizeof(DevCounters) % 8 == 0, "the mirror is copied in 8-byte words");
+
+// kmerco_digest's two sums, after the DevCounters.
+unsigned long long *digest_sums(const kmerco_t *h) {
+    return (unsigned long long *)((char *)h->ctr + sizeof(DevCounters));
+}
+
+// kmerco_digest: the two sums of mixed (index, cell) values, summed per warp
+// and added to the handle's counters (wrapping, so the order does not matter).
+__global__ void digest_kernel(const uint64_t *cells, uint64_t words, unsigned long long *acc) {
+    uint64_t s0 = 0, s1 = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < words;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t c = cells[i];
+        s0 += fmix64(c ^ (i * 0x9E3779B97F4A7C15ull));
+        s1 += fmix64(c + fmix64(i + 1));
+    }
+    for (int o = 16; o; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, (unsigned long long)s0);
+        atomicAdd(acc + 1, (unsigned long long)s1);
+    }
+}
 
 int read_counters(kmerco_t *h) {
     mirror_counters_kernel<<<1, 32, 0, h->stream>>>((const unsigned long long *)h->ctr,
@@ -625,7 +654,7 @@ int kmerco_estimate_bytes(const kmerco_config_t *cfg, uint64_t nreads, uint64_t 
     const uint64_t kw = (uint64_t)t.kw;
     // ensure(): need + need / 4 + 64 elements
     auto grown = [](uint64_t need, uint64_t elem) { return (need + need / 4 + 64) * elem; };
-    uint64_t b = t.G.words * 8 + sizeof(DevCounters);
+    uint64_t b = t.G.words * 8 + kCtrBytes;
     if (host_inputs) b += grown(nbytes, 1) + grown(nreads + 1, 8);
     if (windows) {
         // distinct list and set for every window being a new key
@@ -724,9 +753,9 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
         void *p;
         if ((status = dev_alloc(h, &p, G.words * 8))) break;
         G.cells = (uint64_t *)p;
-        if ((status = dev_alloc(h, &p, sizeof(DevCounters)))) break;
+        if ((status = dev_alloc(h, &p, kCtrBytes))) break;
         h->ctr = (DevCounters *)p;
-        if (cudaHostAlloc((void **)&h->ctr_host, sizeof(DevCounters), cudaHostAllocMapped) !=
+        if (cudaHostAlloc((void **)&h->ctr_host, kCtrBytes, cudaHostAllocMapped) !=
             cudaSuccess) {
             cudaGetLastError();
             h->ctr_host = nullptr;
@@ -738,7 +767,7 @@ int kmerco_create_ex(const kmerco_config_t *cfg, kmerco_t **out) {
             status = KMERCO_ECUDA;
             break;
         }
-        memset(h->ctr_host, 0, sizeof(DevCounters));
+        memset(h->ctr_host, 0, kCtrBytes);
         if (cudaMemsetAsync(G.cells, 0, G.words * 8, h->stream) != cudaSuccess ||
             cudaMemsetAsync(h->ctr, 0, sizeof(DevCounters), h->stream) != cudaSuccess ||
             cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -762,7 +791,7 @@ void kmerco_destroy(kmerco_t *h) {
         if (h->stream) cudaStreamSynchronize(h->stream);
         if (h->out_stream) cudaStreamSynchronize(h->out_stream);
         dev_free(h, h->G.cells, h->G.words * 8);
-        dev_free(h, h->ctr, sizeof(DevCounters));
+        dev_free(h, h->ctr, kCtrBytes);
         dev_free(h, h->table, h->cap * h->kw * 8);
         dev_free(h, h->dlist, h->dlist_cap * h->kw * 8);
         dev_free(h, h->in_bases, h->in_bases_cap);
@@ -1127,6 +1156,24 @@ static int copy_out(kmerco_t *h, void *dst, const void *src, uint64_t bytes) {
     if (bytes == 0) return KMERCO_OK;
     KM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->stream));
     KM_CUDA(cudaStreamSynchronize(h->stream));
+    return KMERCO_OK;
+}
+
+int kmerco_digest(kmerco_t *h, uint64_t *out) {
+    if (!h || !out) return KMERCO_EINVAL;
+    DeviceGuard guard(h->device);
+    unsigned long long *acc = digest_sums(h);
+    KM_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(unsigned long long), h->stream));
+    const uint64_t words = h->G.words;
+    const unsigned grid = (unsigned)std::min<uint64_t>((words + 255) / 256, 152ull * 8);
+    digest_kernel<<<grid, 256, 0, h->stream>>>(h->G.cells, words, acc);
+    KM_CUDA(cudaGetLastError());
+    h->launches += 1;
+    KM_TRY(read_counters(h));
+    const unsigned long long *got =
+        (const unsigned long long *)((const char *)h->ctr_host + sizeof(DevCounters));
+    out[0] = got[0];
+    out[1] = got[1];
     return KMERCO_OK;
 }
 

@@ -21,7 +21,6 @@ from __future__ import annotations
 
 import collections
 import concurrent.futures as cf
-import hashlib
 import threading
 import time
 from dataclasses import dataclass, field
@@ -59,7 +58,7 @@ class JobResult:
     distinct: int
     trustworthy: int
     erroneous: int
-    counters_sha256: str
+    counters_digest: str      # kmerco_digest of the job's countBF (computed on the device)
     trusted: np.ndarray | None
     erroneous_keys: np.ndarray | None
     submitted: float
@@ -254,7 +253,7 @@ class Server:
         h.insert(job.bases, job.offsets)
         h.classify()
         st = h.stats()
-        digest = hashlib.sha256(h.counters().tobytes()).hexdigest()
+        digest = h.digest()
         tr = h.trusted() if job.keep_lists else None
         er = h.erroneous() if job.keep_lists else None
         return JobResult(job.name, st["inserted"], st["distinct"], st["trustworthy"],

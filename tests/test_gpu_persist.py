@@ -56,3 +56,43 @@ def test_set_counters_checks_the_size():
         with pytest.raises(kc.KmercoError) as e:
             kc.kmerco_set_counters(bf.h, np.zeros(w + 1, np.uint64), w + 1)
         assert e.value.status == kc.ESIZE
+
+
+def _fmix64(k):
+    k = np.asarray(k, np.uint64)
+    k ^= k >> np.uint64(33)
+    k *= np.uint64(0xFF51AFD7ED558CCD)
+    k ^= k >> np.uint64(33)
+    k *= np.uint64(0xC4CEB9FE1A85EC53)
+    k ^= k >> np.uint64(33)
+    return k
+
+
+def _digest(cells):
+    # the definition in kmerco.h, on the host: two wrapping sums of mixed
+    # (index, cell) values
+    i = np.arange(len(cells), dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        s0 = _fmix64(cells ^ (i * np.uint64(0x9E3779B97F4A7C15))).sum(dtype=np.uint64)
+        s1 = _fmix64(cells + _fmix64(i + np.uint64(1))).sum(dtype=np.uint64)
+    return int(s0), int(s1)
+
+
+def test_digest_is_its_definition_and_tells_countbfs_apart():
+    b, o = readsim.scaled("tiny", 900, seed_offset=17).generate()
+    with kc.CountBF(21, (1 << 20) + 48, 5, 3, 2) as bf:   # 12 counters per cell, ragged
+        bf.insert(b, o)
+        cells = bf.counters()
+        d = kc.kmerco_digest(bf.h)
+        assert d == _digest(cells)
+        assert kc.kmerco_digest(bf.h) == d                  # deterministic
+        changed = cells.copy()
+        changed[len(changed) // 2] ^= np.uint64(1)           # one counter one step apart
+        kc.kmerco_set_counters(bf.h, changed, len(changed))
+        d2 = kc.kmerco_digest(bf.h)
+        assert d2 == _digest(changed) and d2[0] != d[0] and d2[1] != d[1]
+        swapped = cells.copy()                               # the same cells in another order
+        swapped[[0, 1]] = swapped[[1, 0]]
+        if swapped[0] != swapped[1]:
+            kc.kmerco_set_counters(bf.h, swapped, len(swapped))
+            assert kc.kmerco_digest(bf.h) != d

@@ -31,7 +31,7 @@ def _jobs(n=10, keep=True):
 
 
 def _key(r):
-    return (r.inserted, r.distinct, r.trustworthy, r.erroneous, r.counters_sha256,
+    return (r.inserted, r.distinct, r.trustworthy, r.erroneous, r.counters_digest,
             r.trusted.tobytes(), r.erroneous_keys.tobytes())
 
 
@@ -70,7 +70,7 @@ def test_budget_bounds_what_runs_at_once():
     for r in res + again:
         assert 0 < r.device_bytes <= r.reserved <= budget, r.name
     assert len(res) == len(jobs) and all(r.inserted > 0 for r in res)
-    assert [x.counters_sha256 for x in res] == [x.counters_sha256 for x in again]
+    assert [x.counters_digest for x in res] == [x.counters_digest for x in again]
 
 
 def test_estimate_bounds_the_library():
