@@ -456,8 +456,10 @@ int kmerco_batch_schedule(kmerco_batch_t *b, int schedule, int streams);
 
 /* Classification of every handle of the batch (the results of
  * kmerco_classify on each): every sample's sort, query and split launched
- * on the batch's concurrent streams with one readback before and one after;
- * handle by handle when the batch has not set up its streams yet. */
+ * on the batch's concurrent streams with one readback before and one after
+ * (and a radix sort afterwards of any run of more than 2^22 keys sharing
+ * their top 24 bits); handle by handle when the batch has not set up its
+ * streams yet. */
 int kmerco_batch_classify(kmerco_batch_t *b);
 
 /* Schedule and counters of the batch. */

@@ -939,6 +939,33 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
 
 namespace {
 
+// After the top-bits sort of D keys in alt0 (the big-segment count at
+// nbig_host, read back by the caller): radix-sorts the runs of equal top
+// bits too long for one block, on stream s.  *any: whether there was one.
+int sort_long_runs(kmerco_t *h, uint64_t D, int bits, uint64_t nb, bool *any, cudaStream_t s) {
+    *any = false;
+    if (!nb) return KMERCO_OK;
+    const int kw = h->kw, passes = (bits + kRadixBits - 1) / kRadixBits;
+    const uint64_t nbe = seg_bounds_entries(D, kw);
+    const unsigned long long *big = h->seg_scratch + nbe;
+    std::vector<unsigned long long> list(2 * nb);
+    KM_CUDA(cudaMemcpyAsync(list.data(), big, 2 * nb * 8, cudaMemcpyDeviceToHost, s));
+    KM_CUDA(cudaStreamSynchronize(s));
+    for (uint64_t q = 0; q < nb; ++q) {
+        if (list[2 * q + 1] <= big_segment_max()) continue;
+        uint64_t *range = h->alt0 + list[2 * q] * kw;
+        const uint64_t n_b = list[2 * q + 1];
+        const uint64_t *res = range;
+        KM_CUDA(radix_sort(range, h->alt1 + list[2 * q] * kw, range, n_b, kw, bits,
+                           h->sort_scratch, &res, s));
+        h->launches += 3 * (uint64_t)passes;
+        if (res != range)
+            KM_CUDA(cudaMemcpyAsync(range, res, n_b * kw * 8, cudaMemcpyDeviceToDevice, s));
+        *any = true;
+    }
+    return KMERCO_OK;
+}
+
 // Orders a classification that rewrites the lists (into `words` words) after
 // the result copies still queued: on the device when the lists' buffer is
 // kept, on the host when it must be reallocated under them.
@@ -996,23 +1023,9 @@ int kmerco_classify(kmerco_t *h) {
         KM_TRY(ensure_bucket_host(h));
         KM_CUDA(cudaMemcpyAsync(h->bucket_host, nbig, 8, cudaMemcpyDeviceToHost, h->stream));
         KM_CUDA(cudaStreamSynchronize(h->stream));
-        const uint64_t nb = h->bucket_host[0];
-        if (nb) {   // ... and the few too long for one block: radix sorts of their own
-            std::vector<unsigned long long> list(2 * nb);
-            KM_CUDA(cudaMemcpy(list.data(), big, 2 * nb * 8, cudaMemcpyDeviceToHost));
-            for (uint64_t q = 0; q < nb; ++q) {
-                if (list[2 * q + 1] <= big_segment_max()) continue;
-                uint64_t *range = h->alt0 + list[2 * q] * kw;
-                const uint64_t n_b = list[2 * q + 1];
-                const uint64_t *res = range;
-                KM_CUDA(radix_sort(range, h->alt1 + list[2 * q] * kw, range, n_b, kw, bits,
-                                   h->sort_scratch, &res, h->stream));
-                h->launches += 3 * (uint64_t)passes;
-                if (res != range)
-                    KM_CUDA(cudaMemcpyAsync(range, res, n_b * kw * 8, cudaMemcpyDeviceToDevice,
-                                            h->stream));
-            }
-        }
+        // ... and the few too long for one block: radix sorts of their own
+        bool any;
+        KM_TRY(sort_long_runs(h, D, bits, h->bucket_host[0], &any, h->stream));
         sorted = h->alt0;
     } else if (kw == 1 && bits >= kHistBits + 8 && D > 65536 &&
                D <= (uint64_t)kHistBins * (kBucketCap / 4)) {
@@ -1427,6 +1440,9 @@ int kmerco_merge(kmerco_t *dst, kmerco_t *src) {
 
 // ------------------------------------------------------------------ batches
 constexpr int kBatchStreams = 8;
+// Distinct keys above which a batch sample's classification sorts by the top
+// key bits and segments rather than by a full radix sort.
+constexpr uint64_t kBatchTopSortMin = 1ull << 16;
 
 struct kmerco_batch {
     std::vector<kmerco_t *> h;
@@ -1883,6 +1899,7 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
                                 b->stream));
     KM_CUDA(cudaStreamSynchronize(b->stream));
     std::vector<uint64_t> D(b->n, 0);
+    std::vector<char> top(b->n, 0);   // the sample takes the top-bits sort
     for (int i = 0; i < b->n; ++i) {
         kmerco_t *h = b->h[i];
         if (h->classified) continue;
@@ -1890,6 +1907,14 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
         D[i] = h->ctr_host->distinct;
         if (D[i] >= 0xFFFFFFFFull) return KMERCO_ENOMEM;   // sort tiles index keys with 32 bits
         const int kw = h->kw;
+        // three radix passes and the segments instead of a full radix sort;
+        // the bucket sort is not used here (it reads its histogram back)
+        top[i] = 2 * h->K >= kTopSortBits + 12 && D[i] > kBatchTopSortMin;
+        if (top[i]) {
+            KM_TRY(ensure(h, &h->seg_scratch, &h->seg_scratch_cap,
+                          3 * seg_bounds_entries(D[i], kw) + 1));
+            KM_TRY(ensure_bucket_host(h));
+        }
         KM_TRY(ensure(h, &h->alt0, &h->alt0_cap, D[i] * kw));
         KM_TRY(ensure(h, &h->alt1, &h->alt1_cap, D[i] * kw));
         KM_TRY(ensure(h, &h->est, &h->est_cap, D[i]));
@@ -1912,15 +1937,15 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
     // CUDA graph: replayed while every sample's distinct count and buffers
     // are those it was captured with
     std::vector<uint64_t> key;
-    key.reserve((size_t)b->n * 10);
+    key.reserve((size_t)b->n * 11);
     for (int i = 0; i < b->n; ++i) {
         const kmerco_t *h = b->h[i];
-        const uint64_t fields[10] = {h->classified ? ~0ull : D[i], (uint64_t)h->dlist,
+        const uint64_t fields[11] = {h->classified ? ~0ull : D[i], (uint64_t)h->dlist,
                                      (uint64_t)h->alt0, (uint64_t)h->alt1, (uint64_t)h->est,
                                      (uint64_t)h->split, (uint64_t)h->sort_scratch,
                                      (uint64_t)h->split_scratch, (uint64_t)h->ctr,
-                                     (uint64_t)h->G.cells};
-        key.insert(key.end(), fields, fields + 10);
+                                     (uint64_t)h->G.cells, (uint64_t)h->seg_scratch};
+        key.insert(key.end(), fields, fields + 11);
     }
     if (b->have_cls && key == b->cls_key) {
         KM_CUDA(cudaGraphLaunch(b->cls_exec, b->stream));
@@ -1961,12 +1986,28 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
                 cudaStream_t st = b->aux[k];
                 const int bits = 2 * h->K, passes = (bits + kRadixBits - 1) / kRadixBits;
                 const uint64_t *sorted = h->dlist;
-                KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D[i], h->kw, bits,
-                                   h->sort_scratch, &sorted, st));
+                uint64_t n_launch = D[i] ? 4 : 0;   // query + three split kernels
+                if (top[i]) {   // as in kmerco_classify; long runs are checked below
+                    const int s0 = bits - kTopSortBits;
+                    const uint64_t nbe = seg_bounds_entries(D[i], h->kw);
+                    unsigned long long *bnd = h->seg_scratch, *big = bnd + nbe,
+                                       *nbig = big + 2 * nbe;
+                    KM_CUDA(radix_pass(h->dlist, h->alt0, D[i], h->kw, s0, h->sort_scratch, st));
+                    KM_CUDA(radix_pass(h->alt0, h->alt1, D[i], h->kw, s0 + 8, h->sort_scratch, st));
+                    KM_CUDA(radix_pass(h->alt1, h->alt0, D[i], h->kw, s0 + 16, h->sort_scratch,
+                                       st));
+                    KM_CUDA(top_segment_sort(h->alt0, D[i], h->kw, bits, bnd, big, nbig, st));
+                    KM_CUDA(big_segment_sort(h->alt0, h->alt1, D[i], h->kw, bits, big, nbig, st));
+                    sorted = h->alt0;
+                    n_launch += 12;
+                } else {
+                    KM_CUDA(radix_sort(h->dlist, h->alt0, h->alt1, D[i], h->kw, bits,
+                                       h->sort_scratch, &sorted, st));
+                    n_launch += D[i] > 1 ? 3 * (uint64_t)passes : 0;
+                }
                 KM_CUDA(launch_classify_query(sorted, D[i], h->kw, h->G, h->tau, h->est, st));
                 KM_CUDA(launch_split(sorted, h->est, D[i], h->kw, h->tau, h->split,
                                      h->split_scratch, h->ctr, st));
-                const uint64_t n_launch = (D[i] > 1 ? 3 * (uint64_t)passes : 0) + (D[i] ? 4 : 0);
                 h->launches += n_launch;
                 b->launches += n_launch;
                 h->sorted = sorted;
@@ -2001,11 +2042,36 @@ int kmerco_batch_classify(kmerco_batch_t *b) {
             return st_launch;
         }
     }
-    // one readback of every sample's trustworthy count
-    for (kmerco_t *h : b->h)
+    // one readback of every sample's trustworthy count and, for the samples
+    // sorted by their top bits, of the count of runs too long for one block
+    for (int i = 0; i < b->n; ++i) {
+        kmerco_t *h = b->h[i];
         KM_CUDA(cudaMemcpyAsync(h->ctr_host, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
                                 b->stream));
+        if (top[i]) {
+            const uint64_t nbe = seg_bounds_entries(D[i], h->kw);
+            KM_CUDA(cudaMemcpyAsync(h->bucket_host, h->seg_scratch + 3 * nbe, 8,
+                                    cudaMemcpyDeviceToHost, b->stream));
+        }
+    }
     KM_CUDA(cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        kmerco_t *h = b->h[i];
+        if (!top[i] || !h->bucket_host[0]) continue;
+        // a run of equal top bits beyond one block (at most D / 2^22 of them):
+        // sort it, then split the sample again
+        bool any;
+        KM_TRY(sort_long_runs(h, D[i], 2 * h->K, h->bucket_host[0], &any, b->stream));
+        if (!any) continue;
+        KM_CUDA(launch_classify_query(h->alt0, D[i], h->kw, h->G, h->tau, h->est, b->stream));
+        KM_CUDA(launch_split(h->alt0, h->est, D[i], h->kw, h->tau, h->split, h->split_scratch,
+                             h->ctr, b->stream));
+        h->launches += 4;
+        b->launches += 4;
+        KM_CUDA(cudaMemcpyAsync(h->ctr_host, h->ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost,
+                                b->stream));
+        KM_CUDA(cudaStreamSynchronize(b->stream));
+    }
     for (kmerco_t *h : b->h) {
         if (h->classified) continue;
         h->n_trusted = h->ctr_host->trusted;

@@ -159,3 +159,23 @@ def test_batch_classify_graph_replay():
                 check(g, b, o, 25, alpha, nhash, tau)
     for f in filters:
         f.close()
+
+
+def test_batch_sample_with_a_run_longer_than_one_block():
+    # one sample whose 4.3e6 distinct 31-mers all begin with twelve A's: they
+    # share the top 24 key bits, a run of equal top bits beyond what one
+    # block sorts (2^22 keys), so the batch sorts that run after the graph and
+    # splits the sample again; a small sample rides along
+    st = readsim.Stream(2222)
+    n = (1 << 22) + 100_000
+    tails = readsim.ASCII[st.integers(n * 19, 4).astype(np.uint8)].reshape(n, 19)
+    heads = np.full((n, 12), ord("A"), np.uint8)
+    b1 = np.concatenate([heads, tails], axis=1).reshape(-1)
+    o1 = np.arange(n + 1, dtype=np.uint64) * np.uint64(31)
+    b2, o2 = readsim.random_reads(300, 40, 160, seed=2223)
+    samples = [(b1, o1, 1 << 26, 4, 3, 2), (b2, o2, 1 << 16, 4, 3, 2)]
+    stream = torch.cuda.Stream()
+    results, info = _run_batch(samples, 31, stream)
+    for (b, o, m, alpha, nhash, tau), g in zip(samples, results):
+        check(g, b, o, 31, alpha, nhash, tau, cross_check=False)
+    assert results[0]["stats"]["distinct"] > (1 << 22)
