@@ -206,10 +206,11 @@ void kmerco_destroy(kmerco_t *h);
  * 2^alpha - 1.  The key also joins the handle's distinct-key set.
  * Calls accumulate; order of reads and calls does not change any result.
  * Asynchronous on the handle's stream.  The buffers are sized from the
- * call's window count: host offsets of up to 2^22 reads are checked and
+ * call's window count: host offsets of up to 2^16 reads are checked and
  * summed on the host, so the call does not wait for the device; device
  * offsets, and host offsets of more reads, are summed by a kernel whose
- * result the call waits for.  A call that has to grow the distinct set
+ * result the call waits for (copied ahead of the reads, so the wait is for
+ * the offsets and the kernel only).  A call that has to grow the distinct set
  * also waits for the keys already held.
  * Errors: EINVAL (NULL pointer with nreads > 0, nreads >= 2^32 - 1,
  * decreasing offsets); ENOMEM; ECUDA.

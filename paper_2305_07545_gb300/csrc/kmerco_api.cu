@@ -21,7 +21,7 @@ constexpr int kCopyPieces = 8;   // pieces of a host input copied while earlier 
 // Host offsets of up to this many reads are checked and summed on the host
 // (a few milliseconds at most), so the insert does not wait for the device;
 // larger ones are copied and summed by a kernel, which the call waits for.
-constexpr uint64_t kHostBoundReads = 1ull << 22;
+constexpr uint64_t kHostBoundReads = 1ull << 16;
 
 // The handle's device counters and their pinned mirror hold a DevCounters
 // followed by kmerco_digest's two sums.
