@@ -767,16 +767,24 @@ __global__ void reinsert_kernel(const uint64_t *keys, uint64_t n, uint64_t *tabl
     }
 }
 
-// Exclusive prefix sum of v[0..n) into out[0..n), n <= 2 * kRepartThreads,
-// by the whole block (two entries per thread).
+// Exclusive prefix sum of v[0..n) into out[0..n), n <= E * kRepartThreads,
+// by the whole block (E entries per thread).
+template <int E>
 __device__ __forceinline__ void repart_scan(const unsigned *v, unsigned *out, unsigned n) {
     const unsigned tid = threadIdx.x;
-    const unsigned v0 = 2 * tid < n ? v[2 * tid] : 0u;
-    const unsigned v1 = 2 * tid + 1 < n ? v[2 * tid + 1] : 0u;
+    unsigned x[E], sum = 0;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        x[q] = E * tid + q < n ? v[E * tid + q] : 0u;
+        sum += x[q];
+    }
     unsigned tot;
-    const unsigned off = block_exclusive_scan<unsigned, kRepartThreads>(v0 + v1, tot);
-    if (2 * tid < n) out[2 * tid] = off;
-    if (2 * tid + 1 < n) out[2 * tid + 1] = off + v0;
+    unsigned off = block_exclusive_scan<unsigned, kRepartThreads>(sum, tot);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        if (E * tid + q < n) out[E * tid + q] = off;
+        off += x[q];
+    }
 }
 
 // Split each coarse region's increment codes into slices of 2^slice_shift
@@ -785,7 +793,7 @@ __device__ __forceinline__ void repart_scan(const unsigned *v, unsigned *out, un
 // code is the 16-bit counting lane (counter << slice_shift) | cell of the
 // counting apply, else the 32-bit (cell << 6) | counter.
 template <int MAXF, bool LANES>
-__global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p) {
+__global__ void __launch_bounds__(kRepartThreads, 3) repartition_kernel(PartArgs p) {
     extern __shared__ uint32_t sorted[];   // the tile's codes grouped by slice
     __shared__ unsigned hist[MAXF], start[MAXF], fill[MAXF];
     __shared__ unsigned long long base[MAXF];
@@ -834,7 +842,7 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
             start[tid] = pre;
         }
     } else {
-        repart_scan(hist, start, fpc);
+        repart_scan<(MAXF + kRepartThreads - 1) / kRepartThreads>(hist, start, fpc);
     }
     for (unsigned f = tid; f < fpc; f += kRepartThreads) {
         const unsigned m = hist[f];
@@ -893,7 +901,7 @@ __global__ void __launch_bounds__(kRepartThreads) repartition_kernel(PartArgs p)
 // 32, so no counter straddles the middle of a cell) each update is a 32-bit
 // compare-and-swap on the half-cell that holds the counter.
 template <bool LIMITED, bool HALF>
-__global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
+__global__ void __launch_bounds__(kCasApplyThreads, 3) apply_kernel(ApplyArgs p) {
     extern __shared__ unsigned long long cells_s[];
     const uint64_t s = blockIdx.x;
     const uint64_t w0 = s << p.slice_shift;
@@ -901,21 +909,21 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
     const unsigned nw = (unsigned)min(slice, p.G.words - w0);
     const uint64_t n = p.written[s];
     if (n == 0) return;   // no increments for this slice
-    for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) cells_s[i] = p.G.cells[w0 + i];
+    for (unsigned i = threadIdx.x; i < nw; i += kCasApplyThreads) cells_s[i] = p.G.cells[w0 + i];
     __syncthreads();
     const uint32_t *src = (const uint32_t *)p.codes + s * p.cap;   // 16-byte aligned: cap is a multiple of 4
     const uint32_t wmask = (uint32_t)(slice - 1);
     const uint64_t maxc = p.G.maxc;
     const unsigned alpha = (unsigned)p.G.alpha;
     // eight codes per thread in flight (two 16-byte loads), then their updates
-    constexpr unsigned kStep = kApplyThreads * 8;
+    constexpr unsigned kStep = kCasApplyThreads * 8;
     for (uint64_t i0 = 0; i0 < n; i0 += kStep) {
         uint32_t code[8];
         unsigned valid = 0;
         const uint64_t i = i0 + threadIdx.x * 4ull;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const uint64_t j = i + (uint64_t)h * kApplyThreads * 4;
+            const uint64_t j = i + (uint64_t)h * kCasApplyThreads * 4;
             if (j + 4 <= n) {
                 const uint4 v = __ldcs((const uint4 *)(src + j));
                 code[4 * h] = v.x;
@@ -966,7 +974,7 @@ __global__ void __launch_bounds__(kApplyThreads, 1) apply_kernel(ApplyArgs p) {
         }
     }
     __syncthreads();
-    for (unsigned i = threadIdx.x; i < nw; i += kApplyThreads) p.G.cells[w0 + i] = cells_s[i];
+    for (unsigned i = threadIdx.x; i < nw; i += kCasApplyThreads) p.G.cells[w0 + i] = cells_s[i];
 }
 
 // Counting apply (alpha <= 15): one slice of 2^slice_shift cells per block.
@@ -1154,11 +1162,14 @@ cudaError_t launch_repartition(const PartArgs &p, cudaStream_t s) {
     const dim3 grid((unsigned)tiles, kCoarseBins);
     if (p.lane_codes && ((uint64_t)p.G.eta << p.slice_shift) > (uint64_t)kCountLanes)
         return cudaErrorInvalidValue;   // a lane must fit 16 bits
-    const bool narrow = p.coarse_shift - p.slice_shift <= 6;
-    void (*k)(PartArgs) = narrow ? (p.lane_codes ? repartition_kernel<64, true>
-                                                 : repartition_kernel<64, false>)
-                                 : (p.lane_codes ? repartition_kernel<kMaxFine, true>
-                                                 : repartition_kernel<kMaxFine, false>);
+    // slices per coarse region: up to 64, 1,024 or kMaxFine (2,048)
+    const int fbits = p.coarse_shift - p.slice_shift;
+    void (*k)(PartArgs) =
+        fbits <= 6    ? (p.lane_codes ? repartition_kernel<64, true> : repartition_kernel<64, false>)
+        : fbits <= 10 ? (p.lane_codes ? repartition_kernel<1024, true>
+                                      : repartition_kernel<1024, false>)
+                      : (p.lane_codes ? repartition_kernel<kMaxFine, true>
+                                      : repartition_kernel<kMaxFine, false>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kRepartThreads, smem, s>>>(p);
@@ -1176,7 +1187,7 @@ cudaError_t launch_apply(const ApplyArgs &p, uint64_t nslices, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(8 << kSliceShift));
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)nslices, kApplyThreads, smem, s>>>(p);
+    k<<<(unsigned)nslices, kCasApplyThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

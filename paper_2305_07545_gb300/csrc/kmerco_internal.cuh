@@ -15,13 +15,14 @@ constexpr int kChunk = 2048;               // window starts per insert work unit
 constexpr int kPartChunk = 1024;           // the same in the partitioned update design
 constexpr int kPartMaxHash = 4;            // hashes the partitioned design stages per window
 constexpr int kCoarseBins = 64;            // coarse countBF regions of the partitioned design
-constexpr int kSliceShift = 14;            // 2^14 cells (128 KiB) per shared-memory slice
+constexpr int kSliceShift = 13;            // 2^13 cells (64 KiB) per shared-memory slice
 constexpr int kMaxCoarseShift = 24;        // cell-in-region bits of an increment code
 constexpr int kMaxFine = 1 << (kMaxCoarseShift - kSliceShift);   // slices per coarse region
 constexpr uint64_t kMaxBatchCodes = 1ull << 31;   // increments staged per partitioned pass
 constexpr int kRepartTile = 8192;          // codes per repartition block
 constexpr int kRepartThreads = 512;
-constexpr int kApplyThreads = 1024;
+constexpr int kApplyThreads = 1024;        // counting apply
+constexpr int kCasApplyThreads = 512;      // compare-and-swap apply: three blocks per SM
 constexpr int kHistBits = 16;              // classify: top key bits histogrammed for buckets
 constexpr int kHistTile = 65535;           // keys per histogram block (16-bit counters)
 constexpr int kHistBins = 1 << kHistBits;
