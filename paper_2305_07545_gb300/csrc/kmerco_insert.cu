@@ -899,7 +899,9 @@ __global__ void __launch_bounds__(kRepartThreads, 3) repartition_kernel(PartArgs
 // handle (a retry limit set for testing); the default bound is a constant,
 // which keeps the retry loop measurably faster.  With HALF (alpha divides
 // 32, so no counter straddles the middle of a cell) each update is a 32-bit
-// compare-and-swap on the half-cell that holds the counter.
+// compare-and-swap on the half-cell that holds the counter.  Slices are
+// 64 KiB, three blocks per SM, so one block's slice load and store overlap
+// the other blocks' updates.
 template <bool LIMITED, bool HALF>
 __global__ void __launch_bounds__(kCasApplyThreads, 3) apply_kernel(ApplyArgs p) {
     extern __shared__ unsigned long long cells_s[];

@@ -524,18 +524,32 @@ def test_hbm_budget_is_enforced():
 @pytest.mark.parametrize("K,m,alpha,tau", [(21, 1 << 15, 4, 12), (31, 1 << 20, 4, 3),
                                            (55, 1 << 18, 8, 2)])
 def test_split_then_estimates_on_request(K, m, alpha, tau):
+    _split_then_estimates(K, m, alpha, 4, tau, both_kinds=True)
+
+
+@pytest.mark.parametrize("K,m,alpha,nhash,tau", [(21, 1 << 16, 1, 1, 0), (33, 1 << 18, 2, 5, 1),
+                                                 (64, 1 << 18, 3, 7, 2), (45, 1 << 12, 3, 7, 6)])
+def test_split_only_query_edge_parameters(K, m, alpha, nhash, tau):
+    # one hash and one-bit counters with tau = 0 (every inserted key is
+    # trustworthy); five and seven hashes with a mix of both kinds; tau at the
+    # largest value alpha allows on a saturated countBF
+    _split_then_estimates(K, m, alpha, nhash, tau, both_kinds=False)
+
+
+def _split_then_estimates(K, m, alpha, nhash, tau, both_kinds):
     # classify reads a key's counters only until one is at or below tau (that
     # decides "erroneous"); the lists must be exact at once, and the full
     # Algorithm 5 estimates of every key when they are asked for afterwards
     b, o = readsim.scaled("tiny", 1500, seed_offset=400 + K).generate()
-    with kc.CountBF(K, m, alpha, 4, tau, update_mode=kc.UPDATE_PARTITIONED) as bf:
+    mode = kc.UPDATE_PARTITIONED if nhash <= 4 else kc.UPDATE_ATOMIC
+    with kc.CountBF(K, m, alpha, nhash, tau, update_mode=mode) as bf:
         bf.insert(_dev(b), _dev(o))
         bf.classify()
         st = bf.stats()
         trusted, erroneous = bf.trusted(), bf.erroneous()
         keys, est = bf.distinct()
         keys2, est2 = bf.distinct()
-    ref = oracle.run(b, o, K, st["m_actual"], alpha, 4, tau)
+    ref = oracle.run(b, o, K, st["m_actual"], alpha, nhash, tau)
     thi, tlo = _split_keys(trusted, K)
     ehi, elo = _split_keys(erroneous, K)
     assert np.array_equal(tlo, ref.distinct_lo[ref.trusted_mask])
@@ -544,6 +558,6 @@ def test_split_then_estimates_on_request(K, m, alpha, tau):
     assert np.array_equal(ehi, ref.distinct_hi[~ref.trusted_mask])
     assert np.array_equal(est.astype(np.uint64), ref.est)
     assert np.array_equal(est2, est) and np.array_equal(keys2, keys)
-    # both kinds of keys occur, and erroneous keys with estimates below tau
-    assert ref.trusted_mask.any() and (~ref.trusted_mask).any()
-    assert (ref.est[~ref.trusted_mask] < tau).any()
+    if both_kinds:   # both kinds of keys occur, and erroneous keys with estimates below tau
+        assert ref.trusted_mask.any() and (~ref.trusted_mask).any()
+        assert (ref.est[~ref.trusted_mask] < tau).any()
