@@ -23,6 +23,11 @@ constexpr int kCopyPieces = 8;   // pieces of a host input copied while earlier 
 // larger ones are copied and summed by a kernel, which the call waits for.
 constexpr uint64_t kHostBoundReads = 1ull << 16;
 
+// Distinct one-word keys above which classification takes the bucket sort
+// (its histogram readback and host-side merge cost more than a full radix
+// sort of a smaller set).
+constexpr uint64_t kBucketSortMin = 1ull << 20;
+
 // The handle's device counters and their pinned mirror hold a DevCounters
 // followed by kmerco_digest's two sums.
 constexpr size_t kCtrBytes = sizeof(DevCounters) + 2 * sizeof(unsigned long long);
@@ -673,7 +678,7 @@ int kmerco_estimate_bytes(const kmerco_config_t *cfg, uint64_t nreads, uint64_t 
         b += 2 * grown(D * kw, 8) + grown(D, 4) + grown(D * kw, 8) +
              grown(sort_scratch_words(D, kw), 4) + grown(split_scratch_words(D), 8);
         if (use_top_sort(D, t.kw, 2 * t.K)) b += grown(3 * seg_bounds_entries(D, t.kw) + 1, 8);
-        if (kw == 1 && 2 * t.K >= kHistBits + 8 && D > 65536)   // the bucket sort may run
+        if (kw == 1 && 2 * t.K >= kHistBits + 8 && D > kBucketSortMin)   // the bucket sort may run
             b += grown(kBucketHostWords + kHistBins, 8) +
                  grown(bucket_hist_blocks(D) * kHistBins, 2);
     }
@@ -1027,7 +1032,7 @@ int kmerco_classify(kmerco_t *h) {
         bool any;
         KM_TRY(sort_long_runs(h, D, bits, h->bucket_host[0], &any, h->stream));
         sorted = h->alt0;
-    } else if (kw == 1 && bits >= kHistBits + 8 && D > 65536 &&
+    } else if (kw == 1 && bits >= kHistBits + 8 && D > kBucketSortMin &&
                D <= (uint64_t)kHistBins * (kBucketCap / 4)) {
         // Bucket sort: histogram of the top kHistBits key bits, adjacent bins
         // merged into super-buckets of at most kBucketCap keys, each sorted in

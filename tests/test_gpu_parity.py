@@ -169,19 +169,21 @@ def test_partitioned_overflow_falls_back_exactly():
 def test_sort_bucket_larger_than_shared_memory():
     # 20,000 distinct 31-mers that all begin with AAAAAAA share the top 14 key
     # bits: one histogram bin holds more keys than a block sorts in shared
-    # memory, so the classification sort takes its radix-sort fallback
+    # memory, so the classification sort takes its radix-sort fallback (about
+    # 1.1e6 more keys put the set in the bucket sort's range)
     st = readsim.Stream(77)
     n = 20000
     tails = readsim.ASCII[st.integers(n * 24, 4).astype(np.uint8)].reshape(n, 24)
     heads = np.full((n, 7), ord("A"), np.uint8)
     b1 = np.concatenate([heads, tails], axis=1).reshape(-1)
     o1 = np.arange(n + 1, dtype=np.uint64) * np.uint64(31)
-    b2, o2 = readsim.random_reads(2000, 80, 150, seed=78)
+    b2, o2 = readsim.random_reads(10000, 130, 150, seed=78)
     b = np.concatenate([b1, b2])
     o = np.concatenate([o1, o2[1:] + o1[-1]])
     g = gpu_run(b, o, 31, 1 << 22, 4, 4, 2)
     ref = check(g, b, o, 31, 4, 4, 2)
     assert int(np.count_nonzero((ref.distinct_lo >> np.uint64(48)) == 0)) > 16384
+    assert len(ref.distinct_lo) > (1 << 20)
 
 
 @pytest.mark.parametrize("K", [31, 55])
