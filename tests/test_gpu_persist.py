@@ -26,9 +26,11 @@ def test_save_load_round_trip(tmp_path, K, opts):
     with kc.CountBF(K, 1 << 18, 4, 3, 2, **opts) as bf:
         bf.insert(_dev(b), _dev(o))
         a = _snapshot(bf)
+        da = bf.digest()
         bf.save(str(tmp_path / "bf.npz"))
     with kc.CountBF.load(str(tmp_path / "bf.npz")) as bf2:
         c = _snapshot(bf2)
+        assert bf2.digest() == da          # the same countBF, 2-D geometries included
     for key in ("counters", "keys", "est", "trusted", "erroneous"):
         assert np.array_equal(a[key], c[key]), key
     assert c["stats"]["distinct"] == a["stats"]["distinct"]

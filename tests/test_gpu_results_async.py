@@ -82,3 +82,40 @@ def test_async_lists_one_list_only():
         kc.kmerco_sync(bf.h)
     assert nt == int(ref.trusted_mask.sum())
     assert np.array_equal(er[:ne].numpy().view(np.uint64), ref.distinct_lo[~ref.trusted_mask])
+
+
+def test_async_lists_of_batch_handles():
+    # handles classified together by a batch: each one's lists copied on its
+    # own result stream, then a second batch classification (which must wait
+    # for those copies before it rewrites the lists) of new inputs
+    stream = torch.cuda.Stream()
+    specs = [(readsim.scaled("tiny", 400 + 300 * i, seed_offset=500 + i).generate(), 1 << 18)
+             for i in range(3)]
+    filters = [kc.CountBF(21, m, 4, 3, 2, stream=stream.cuda_stream) for _, m in specs]
+
+    def dev(a):
+        return torch.from_numpy(a.view(np.int64) if a.dtype == np.uint64 else a).cuda()
+
+    with kc.Batch(filters) as batch:
+        for rnd in range(2):
+            inputs = specs if rnd == 0 else specs[::-1]   # other samples in each handle
+            d = [(dev(b), dev(o)) for (b, o), _ in inputs]
+            torch.cuda.synchronize()
+            batch.insert([x[0] for x in d], [x[1] for x in d])
+            batch.classify()
+            outs = []
+            for f in filters:
+                nt = kc.kmerco_get_trusted(f.h)
+                ne = kc.kmerco_get_erroneous(f.h)
+                tr = torch.empty(max(nt, 1), dtype=torch.int64).pin_memory()
+                er = torch.empty(max(ne, 1), dtype=torch.int64).pin_memory()
+                assert kc.kmerco_get_lists_async(f.h, tr, nt, er, ne) == (nt, ne)
+                outs.append((tr, er, nt, ne))
+            for f, ((b, o), _), (tr, er, nt, ne) in zip(filters, inputs, outs):
+                kc.kmerco_sync(f.h)
+                ref = oracle.run(b, o, 21, 1 << 18, 4, 3, 2)
+                mask = ref.trusted_mask
+                assert np.array_equal(tr[:nt].numpy().view(np.uint64), ref.distinct_lo[mask])
+                assert np.array_equal(er[:ne].numpy().view(np.uint64), ref.distinct_lo[~mask])
+    for f in filters:
+        f.close()

@@ -67,6 +67,7 @@ def test_sharded_count_equals_whole_sample(K, m, world, mode):
         assert (r.windows, r.inserted, r.distinct) == (ref.n_windows, ref.n_inserted,
                                                        len(ref.distinct_lo))
         assert r.trustworthy == int(m_tr.sum())
+    assert len({r.owner.digest() for r in res}) == 1
     # each owner's estimates are Algorithm 5 on the merged countBF
     for r in res:
         keys, est = r.owner.distinct()
