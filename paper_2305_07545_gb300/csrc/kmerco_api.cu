@@ -522,6 +522,14 @@ int issue_host_copy(kmerco_t *h, const uint8_t *src, uint8_t *dst, uint64_t nbyt
     return KMERCO_OK;
 }
 
+// Window starts per work unit of an insert call: the partitioned design's
+// chunk, else kChunk, or kSmallChunk when the call's chunks of kChunk would
+// not give every resident block of the GPU one (small inputs).
+uint64_t insert_chunk(const kmerco_t *h, const PartPlan &pp, uint64_t nbytes) {
+    if (pp.part) return kPartChunk;
+    return (nbytes + kChunk - 1) / kChunk < (uint64_t)h->grid_atomic ? kSmallChunk : kChunk;
+}
+
 // All device work of one insert call on stream s, without host
 // synchronisation (so it can be captured): first reads of the chunks, then
 // per pass the insert kernel and, in the partitioned design, repartition and
@@ -532,7 +540,7 @@ int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
                          const PartBufs &pb, cudaStream_t s, uint64_t &launches,
                          const HostCopy *hc = nullptr) {
     const uint64_t nbytes = a.last - a.first;
-    const uint64_t chunk = pp.part ? kPartChunk : kChunk;
+    const uint64_t chunk = insert_chunk(h, pp, nbytes);
     const uint64_t nchunks = (nbytes + chunk - 1) / chunk;
     // chunk ranges of the insert launches: per pass, pieces when copying
     const uint64_t q = hc && pp.passes <= (uint64_t)kCopyPieces
@@ -569,7 +577,7 @@ int launch_sample_insert(const kmerco_t *h, InsertArgs a, const PartPlan &pp,
             }
             a.chunk_begin = cut[r];
             a.nchunks = cut[r + 1];
-            KM_CUDA(launch_insert(a, grid, s));
+            KM_CUDA(launch_insert(a, grid, (int)chunk, s));
             launches += a.nchunks > a.chunk_begin ? 1 : 0;
         }
         if (!pp.part) continue;
@@ -671,7 +679,7 @@ int kmerco_estimate_bytes(const kmerco_config_t *cfg, uint64_t nreads, uint64_t 
             b += grown(pp.coarse_words(), 4) + grown(pp.ctr_words(), 8);
             if (pp.repart) b += grown(pp.fine_words(), 4);
         }
-        const uint64_t chunk = pp.part ? kPartChunk : kChunk;
+        const uint64_t chunk = pp.part ? kPartChunk : kSmallChunk;   // the most chunks
         b += grown((nbytes + chunk - 1) / chunk, 4);
         // classification of at most `windows` distinct keys
         const uint64_t D = windows;
@@ -930,7 +938,7 @@ int kmerco_insert(kmerco_t *h, const char *bases, const uint64_t *offsets, uint6
          (pp.repart && ensure(h, &h->fine, &h->fine_alloc, pp.fine_words()) != KMERCO_OK) ||
          ensure(h, &h->part_ctr, &h->part_ctr_alloc, pp.ctr_words()) != KMERCO_OK))
         pp = PartPlan();   // the atomic design when the buffers cannot be had
-    const uint64_t chunk = pp.part ? kPartChunk : kChunk;
+    const uint64_t chunk = insert_chunk(h, pp, nbytes);
     KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, (nbytes + chunk - 1) / chunk));
     const InsertArgs a = sample_args(h, d_bases, d_off, nreads, first, last);
     KM_CUDA(cudaEventRecord(h->ev[0], h->stream));
@@ -1789,7 +1797,7 @@ int kmerco_batch_insert(kmerco_batch_t *b, const char *const *bases,
         if (h->whole_file)   // the sample's reads are one sequence
             bound = bo[2] - bo[1] >= (uint64_t)h->K ? bo[2] - bo[1] - h->K + 1 : 0;
         KM_TRY(ensure_set_capacity(h, bound));
-        const uint64_t most = (bo[2] - bo[1] + 1023) / 1024;   // chunks at the smallest chunk size
+        const uint64_t most = (bo[2] - bo[1] + kSmallChunk - 1) / kSmallChunk;   // chunks at the smallest chunk size
         KM_TRY(ensure(h, &h->first_read, &h->first_read_cap, most ? most : 1));
         b->plans[i] = plan_partition(h, bound, bo[2] - bo[1]);
         b->load[i] = bound;

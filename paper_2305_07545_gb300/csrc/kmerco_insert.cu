@@ -1076,7 +1076,10 @@ cudaError_t insert_variant(const InsertArgs *a, unsigned g, cudaStream_t s, int 
 // part: 0 atomic design; 1 partitioned, region bits inside the codes
 // (coarse_shift <= 20); 2 partitioned, regions beside the codes.
 cudaError_t dispatch_insert(const InsertArgs *a, int kw, int part, unsigned g, cudaStream_t s,
-                            int *per_sm) {
+                            int *per_sm, int chunk = kChunk) {
+    if (part == 0 && chunk == kSmallChunk)
+        return kw == 1 ? insert_variant<1, kSmallChunk, 0>(a, g, s, per_sm)
+                       : insert_variant<2, kSmallChunk, 0>(a, g, s, per_sm);
     if (part == 1 && kw == 1) return insert_variant<1, kPartChunk, 1>(a, g, s, per_sm);
     if (part == 1) return insert_variant<2, kPartChunk, 1>(a, g, s, per_sm);
     if (part == 2 && kw == 1) return insert_variant<1, kPartChunk, 2>(a, g, s, per_sm);
@@ -1206,12 +1209,13 @@ cudaError_t launch_apply_count(const ApplyArgs &p, uint64_t nslices, cudaStream_
     return cudaGetLastError();
 }
 
-cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s) {
+cudaError_t launch_insert(const InsertArgs &a, int grid, int chunk, cudaStream_t s) {
     if (a.nchunks <= a.chunk_begin) return cudaSuccess;
     const uint64_t n = a.nchunks - a.chunk_begin;
     const uint64_t g = n < (uint64_t)grid ? n : (uint64_t)grid;
     const int part = !a.part ? 0 : a.coarse_shift <= 20 ? 1 : 2;
-    return dispatch_insert(&a, a.K <= 32 ? 1 : 2, part, (unsigned)g, s, nullptr);
+    if ((part ? kPartChunk : chunk) != chunk) return cudaErrorInvalidValue;
+    return dispatch_insert(&a, a.K <= 32 ? 1 : 2, part, (unsigned)g, s, nullptr, chunk);
 }
 
 cudaError_t launch_reinsert(const uint64_t *keys, uint64_t n, int kw, uint64_t *table,

@@ -12,6 +12,7 @@ namespace countbf {
 constexpr uint64_t kEmptyKey = ~0ull;      // empty slot of the distinct-key set;
                                            // no canonical key is all ones
 constexpr int kChunk = 2048;               // window starts per insert work unit
+constexpr int kSmallChunk = 512;           // the same for inputs too small to fill the GPU
 constexpr int kPartChunk = 1024;           // the same in the partitioned update design
 constexpr int kPartMaxHash = 4;            // hashes the partitioned design stages per window
 constexpr int kCoarseBins = 64;            // coarse countBF regions of the partitioned design
@@ -343,7 +344,9 @@ cudaError_t launch_window_bound(const uint64_t *offsets, uint64_t nreads, int K,
 cudaError_t launch_first_read(const uint64_t *offsets, uint64_t nreads, uint64_t first,
                               uint64_t nchunks, uint64_t chunk, uint32_t *first_read,
                               cudaStream_t s);
-cudaError_t launch_insert(const InsertArgs &a, int grid, cudaStream_t s);
+// chunk: the window starts per work unit the call was planned with (kChunk
+// or kSmallChunk in the atomic design, kPartChunk in the partitioned one).
+cudaError_t launch_insert(const InsertArgs &a, int grid, int chunk, cudaStream_t s);
 // Resident insert blocks per SM; part: 0 atomic design, 1 partitioned with
 // region bits inside the codes (coarse_shift <= 20), 2 partitioned (wide).
 int insert_blocks_per_sm(int kw, int part);
